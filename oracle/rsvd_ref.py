@@ -1,0 +1,205 @@
+"""Plain FP64 restatement of the paper's image-alignment computation.
+
+Conventions (each a reading of the paper, listed with its justification in
+the design notes):
+
+* Polar samples F[..., r, q] = F_hat(k_r, psi_q), psi_q = 2 pi q / Q,
+  dpsi = 2 pi / Q; radial quadrature weights w_r for the k dk measure.
+* Fourier-Bessel coefficients (section 2.3, discrete form of eq. aqk) use the
+  1/(2 pi) of the continuous definition: a(k_r, q) = (1/Q) sum_q' F(k_r, psi_q')
+  exp(-i q psi_q'), q taken periodically in [0, Q).
+* Rotation (section 2.2, eq. rotation_definition): R_gamma F(k, psi) =
+  F(k, psi - gamma); X(gamma) = <A, R_gamma B> with the conjugate on A.
+* Translation (section 5, eq. Image_single_cost_with_translations names
+  T_delta without a formula): (T_delta A)(x) = A(x - delta), hence
+  (T_delta A)^(k) = A^(k) exp(-i k . delta); scores translate the image.
+* Principal-image-rings (section 3.2) scale ring r by sqrt(w_r); the constant
+  sqrt(dpsi) of eta_r is dropped so that rank H = R reproduces
+  eq. image_innerproduct exactly (the 2 pi of its Step 1 is kept).
+* Radial kernel (section 3.3, eq. Image_simple_kern with the sqrt(w_r w_r')
+  of eq. Image_single_kern kept; section 3.4, eq. image_cost_and_kern as a
+  mean over the N_B templates); its constant (2 pi)^3 / (4 sigma_hat^2) is
+  dropped because it does not change the principal vectors.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import logsumexp
+
+
+# ---------------------------------------------------------------------------
+# Section 2.3: discrete Fourier-Bessel coefficients of each image-ring.
+# ---------------------------------------------------------------------------
+def fb_coefficients(F: np.ndarray) -> np.ndarray:
+    """a(k_r, q) = sum_q' F(k_r, psi_q') exp(-i q psi_q') dpsi / (2 pi) over the
+    last axis (trapezoidal angular quadrature, section 2.3)."""
+    Q = F.shape[-1]
+    return np.fft.fft(F, axis=-1) / Q
+
+
+# ---------------------------------------------------------------------------
+# Section 5 (translations): T_delta applied in frequency space.
+# ---------------------------------------------------------------------------
+def translate(F: np.ndarray, k: np.ndarray, deltas: np.ndarray) -> np.ndarray:
+    """F [n, R, Q] -> [n, T, R, Q], sample (r, q) multiplied by
+    exp(-i k_r (delta_x cos psi_q + delta_y sin psi_q))."""
+    Q = F.shape[-1]
+    psi = 2.0 * math.pi * np.arange(Q) / Q
+    proj = deltas[:, 0][:, None] * np.cos(psi)[None, :] + deltas[:, 1][:, None] * np.sin(psi)[None, :]
+    phase = np.exp(-1j * k[None, :, None] * proj[:, None, :])  # [T, R, Q]
+    return F[:, None, :, :] * phase[None]
+
+
+# ---------------------------------------------------------------------------
+# Section 2.2: X(gamma) = <A_hat, R_gamma B_hat> = int A^dagger(k,psi) B(k,psi-gamma) k dk dpsi,
+# discretised with the polar quadrature of section 2.3 (weights w_r dpsi) and
+# evaluated by brute force at every grid angle gamma_m = 2 pi m / Q.
+# ---------------------------------------------------------------------------
+def scores_direct(A_t: np.ndarray, B: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """A_t [nA, T, R, Q] (translated images), B [nB, R, Q] ->
+    complex X [nA, T, nB, Q]; X[..., m] = sum_r w_r dpsi sum_q'
+    conj(A_t(r, q')) B(r, (q' - m) mod Q)."""
+    nA, T, R, Q = A_t.shape
+    nB = B.shape[0]
+    dpsi = 2.0 * math.pi / Q
+    Aw = (np.conj(A_t) * (w[None, None, :, None] * dpsi)).reshape(nA * T, R * Q)
+    X = np.empty((nA * T, nB, Q), dtype=np.complex128)
+    for m in range(Q):
+        Bm = np.roll(B, m, axis=-1)  # Bm[..., q'] = B[..., (q' - m) mod Q]
+        X[:, :, m] = Aw @ Bm.reshape(nB, R * Q).T
+    return X.reshape(nA, T, nB, Q)
+
+
+# ---------------------------------------------------------------------------
+# Section 2.4, eq. image_innerproduct: Step 1 then Step 2 with all R rings.
+# ---------------------------------------------------------------------------
+def scores_fb(A_t: np.ndarray, B: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Uncompressed Fourier-Bessel route. Step 1: X_hat(q) = 2 pi sum_r w_r
+    conj(a(k_r, q)) b(k_r, q). Step 2: X(gamma_m) = sum_q exp(-i q gamma_m) X_hat(q).
+    Returns complex X [nA, T, nB, Q]."""
+    a = fb_coefficients(A_t)  # [nA, T, R, Q]
+    b = fb_coefficients(B)  # [nB, R, Q]
+    Xhat = 2.0 * math.pi * np.einsum("ntrq,r,jrq->ntjq", np.conj(a), w, b)
+    return np.fft.fft(Xhat, axis=-1)
+
+
+# ---------------------------------------------------------------------------
+# Sections 3.3-3.4: ring-ring kernel C and its principal vectors.
+# ---------------------------------------------------------------------------
+def radial_kernel(B: np.ndarray, w: np.ndarray, return_complex: bool = False) -> np.ndarray:
+    """C_{r r'} = (1/N_B) sum_j sum_{q != 0} conj(beta_j(r, q)) beta_j(r', q),
+    beta_j(r, q) = sqrt(w_r) b_j(k_r, q) (eq. Image_simple_kern averaged over
+    templates as in eq. image_cost_and_kern). Returns the real part unless
+    return_complex (for real images the imaginary part vanishes)."""
+    b = fb_coefficients(B)  # [nB, R, Q]
+    beta = np.sqrt(w)[None, :, None] * b
+    beta = beta[:, :, 1:]  # drop q = 0
+    C = np.einsum("jrq,jsq->rs", np.conj(beta), beta) / B.shape[0]
+    return C if return_complex else C.real
+
+
+def principal_vectors(C: np.ndarray, H: int) -> tuple[np.ndarray, np.ndarray]:
+    """Principal vectors u_1..u_H of the symmetric kernel C (section 3.3):
+    eigenvectors in order of decreasing eigenvalue, each signed so that its
+    entry of largest magnitude is positive. Returns (U [R, H], eigenvalues [R]
+    in decreasing order)."""
+    lam, V = np.linalg.eigh(C)
+    order = np.argsort(lam)[::-1]
+    lam, V = lam[order], V[:, order]
+    idx = np.argmax(np.abs(V), axis=0)
+    sgn = np.sign(V[idx, np.arange(V.shape[1])])
+    sgn[sgn == 0] = 1.0
+    V = V * sgn[None, :]
+    return V[:, :H].copy(), lam
+
+
+# ---------------------------------------------------------------------------
+# Section 3.2 + eq. image_innerproduct_pm: principal-image-rings and the
+# compressed two-step score.
+# ---------------------------------------------------------------------------
+def compress(F_t: np.ndarray, U: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """[u_h^T a](q) = sum_r U_{r h} sqrt(w_r) a(k_r, q) for every q in [0, Q).
+    F_t [..., R, Q] -> [..., H, Q]."""
+    a = fb_coefficients(F_t)
+    Wt = U * np.sqrt(w)[:, None]  # [R, H]
+    return np.einsum("rh,...rq->...hq", Wt, a)
+
+
+def scores_compressed(a_c: np.ndarray, b_c: np.ndarray) -> np.ndarray:
+    """eq. image_innerproduct_pm. Step 1: X_hat(q) = 2 pi sum_h conj([u_h^T a](q))
+    [u_h^T b](q). Step 2: X(gamma_m) = sum_q exp(-i q gamma_m) X_hat(q).
+    a_c [nA, T, H, Q], b_c [nB, H, Q] -> complex X [nA, T, nB, Q]."""
+    Xhat = 2.0 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(a_c), b_c)
+    return np.fft.fft(Xhat, axis=-1)
+
+
+# ---------------------------------------------------------------------------
+# Section 2.7 (gamma_opt = argmax X) with the translations of section 5.
+# ---------------------------------------------------------------------------
+def align_best(X: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """X real [nA, T, nB, Q] -> best [nA, nB] = max over (t, m) and
+    arg [nA, nB] = t * Q + m of the first maximum (smallest flat index)."""
+    nA, T, nB, Q = X.shape
+    flat = np.transpose(X, (0, 2, 1, 3)).reshape(nA, nB, T * Q)
+    arg = np.argmax(flat, axis=-1)
+    best = np.take_along_axis(flat, arg[..., None], axis=-1)[..., 0]
+    return best, arg
+
+
+# ---------------------------------------------------------------------------
+# Section 2.6 likelihood, marginalised over (gamma, delta, template): the
+# log-sum-exp alignment loss L = sum_n log sum_{j,t,m} exp(X / sigma^2).
+# ---------------------------------------------------------------------------
+def lse_pair_partials(X: np.ndarray, inv_sigma2: float) -> np.ndarray:
+    """Per (image, template): log sum_{t, m} exp(X * inv_sigma2). X [nA, T, nB, Q]."""
+    return logsumexp(np.transpose(X, (0, 2, 1, 3)) * inv_sigma2, axis=(2, 3))
+
+
+def lse_loss(X: np.ndarray, inv_sigma2: float) -> tuple[float, np.ndarray]:
+    """Returns (sum_n L_n, L [nA]) with L_n = log sum_{j, t, m} exp(X * inv_sigma2)."""
+    Ln = logsumexp(X * inv_sigma2, axis=(1, 2, 3))
+    return float(Ln.sum()), Ln
+
+
+def lse_loss_grad(images: np.ndarray, templates: np.ndarray, k: np.ndarray, w: np.ndarray,
+                  deltas: np.ndarray, U: np.ndarray, inv_sigma2: float):
+    """Loss and its gradient with respect to the polar samples of the images
+    and of the templates, U held fixed. Gradients follow the convention
+    G = dL/dRe + i dL/dIm. Chain, in reverse order of the forward steps:
+
+    dL/dX = inv_sigma2 * softmax_{(j,t,m)}(X * inv_sigma2) per image;
+    X(m) = Re sum_q exp(-2 pi i q m / Q) X_hat(q)
+        => G_Xhat(q) = sum_m exp(+2 pi i q m / Q) dL/dX(m);
+    X_hat = 2 pi sum_h conj(a_h) b_h
+        => G_b_h = 2 pi sum_{n,t} a_h G_Xhat,  G_a_h = 2 pi sum_j b_h conj(G_Xhat);
+    a_h(q) = sum_r U_rh sqrt(w_r) a(r, q)  => G_a(r, q) = sqrt(w_r) sum_h U_rh G_a_h(q);
+    a(r, q) = (1/Q) sum_psi F(r, psi) exp(-2 pi i q psi / Q)
+        => G_F(r, psi) = (1/Q) sum_q exp(+2 pi i q psi / Q) G_a(r, q);
+    F_t = F * phi_t  => G_F = sum_t conj(phi_t) G_F_t.
+    """
+    nA, R, Q = images.shape
+    A_t = translate(images, k, deltas)  # [nA, T, R, Q]
+    a_c = compress(A_t, U, w)  # [nA, T, H, Q]
+    b_c = compress(templates, U, w)  # [nB, H, Q]
+    X = scores_compressed(a_c, b_c).real  # [nA, T, nB, Q]
+    loss, Ln = lse_loss(X, inv_sigma2)
+    P = np.exp(X * inv_sigma2 - Ln[:, None, None, None]) * inv_sigma2  # dL/dX
+    G_Xhat = np.fft.ifft(P, axis=-1) * Q  # sum_m exp(+2 pi i q m / Q) P(m)
+    G_bc = 2.0 * math.pi * np.einsum("nthq,ntjq->jhq", a_c, G_Xhat)
+    G_ac = 2.0 * math.pi * np.einsum("jhq,ntjq->nthq", b_c, np.conj(G_Xhat))
+    Wt = U * np.sqrt(w)[:, None]
+
+    def back_compress(G_c):
+        G_a = np.einsum("rh,...hq->...rq", Wt, G_c)
+        return np.fft.ifft(G_a, axis=-1)  # (1/Q) sum_q exp(+...) G_a
+
+    G_At = back_compress(G_ac)  # [nA, T, R, Q]
+    psi = 2.0 * math.pi * np.arange(Q) / Q
+    proj = deltas[:, 0][:, None] * np.cos(psi)[None, :] + deltas[:, 1][:, None] * np.sin(psi)[None, :]
+    phase = np.exp(-1j * k[None, :, None] * proj[:, None, :])  # [T, R, Q]
+    G_images = np.einsum("ntrq,trq->nrq", G_At, np.conj(phase))
+    G_templates = back_compress(G_bc)
+    return loss, G_images, G_templates
