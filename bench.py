@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the radial-SVD image-alignment hot path.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+compress the N_A images at all T translations and the N_B templates
+(translate, project onto the H principal vectors, angular FFT), then the fused
+contraction + FFT over q + max/argmax over (gamma, delta) for every
+(image, template) pair. The principal vectors (radial-SVD precompute) are
+built once before timing and reported separately.
+
+Workload (default): 128x128-pixel Gaussian-blob images, 64 rings, Q = 256,
+N_B = 1024 templates, N_A = 8192 images per GPU at SNR 0.05, T = 9
+translations (3x3, 1 px), H = 12, FP32. The 1.07 GB of polar images per GPU
+is larger than L2, so no L2 flush is needed between steps.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run (one rank per GPU, NCCL used only for the barrier and
+the max-over-ranks timing; each rank scores its own images: weak scaling).
+--impl reference times the FP64 oracle on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair·translation·rotation scores/sec"
+UNIT = "scores/s"
+
+# ---------------------------------------------------------------------------
+# FP64 oracle on host cores (cpu_baseline leg and --impl reference only)
+# ---------------------------------------------------------------------------
+_W = {}
+
+
+def _oracle_init(k, w, deltas, U, b_c):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    _W.update(k=k, w=w, deltas=deltas, U=U, b_c=b_c)
+
+
+def _oracle_images(images):
+    """Oracle path for a chunk of images: translate, compress, compressed
+    two-step score against all templates, max/argmax. Returns (best, arg)."""
+    import oracle as O
+
+    A_t = O.translate(images, _W["k"], _W["deltas"])
+    a_c = O.compress(A_t, _W["U"], _W["w"])
+    X = O.scores_compressed(a_c, _W["b_c"]).real
+    return O.align_best(X)
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _oracle_pool(k, w, deltas, U, b_c):
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    n = _cores()
+    return ctx.Pool(n, initializer=_oracle_init, initargs=(k, w, deltas, U, b_c)), n
+
+
+def _time_oracle(pool, images, per_worker):
+    """Wall time of the oracle over `images` split one chunk per task."""
+    chunks = [images[i:i + per_worker] for i in range(0, images.shape[0], per_worker)]
+    t0 = time.perf_counter()
+    out = pool.map(_oracle_images, chunks)
+    return time.perf_counter() - t0, out
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 10:
+                    continue
+                if self.uuid and f[1] != self.uuid:
+                    continue
+                rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload_desc(cfg):
+    return (f"Gaussian-blob images {cfg['N']}x{cfg['N']} px, R={cfg['R']} rings, Q={cfg['Q']}, "
+            f"N_B={cfg['N_B']} templates, N_A={cfg['N_A']} images/GPU, T={cfg['T_side'] ** 2} translations "
+            f"({cfg['T_side']}x{cfg['T_side']}, 1 px), H={cfg['H']}, SNR {cfg['snr']}")
+
+
+def _alg_flops_per_pair(H, Q):
+    """Algorithmic FP32 work per (image, translation, template) pair: the
+    half-spectrum contraction (8 flops per complex multiply-add, Q/2+1
+    frequencies), a C2R FFT of length Q (2.5 Q log2 Q) and the reduction
+    (2 ops per score)."""
+    return 8 * H * (Q // 2 + 1) + 2.5 * Q * math.log2(Q) + 2 * Q
+
+
+def _load_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path)).get(kernel_key)
+        if not d:
+            return None
+        h = hashlib.sha256()
+        for f in d["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return d["bytes_per_launch"] if h.hexdigest() == d["sha256"] else None
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2202_07235_gb300 as P
+    from synthetic import CONFIGS, make_workload_torch
+
+    rank, world, local = _dist_env()
+    cfg = dict(CONFIGS[args.config])
+    if args.n_images:
+        cfg["N_A"] = args.n_images
+
+    # the oracle pool is started before the first GPU call (spawned workers)
+    want_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    P.lib()
+
+    N_A, N_B, Q, H, R = cfg["N_A"], cfg["N_B"], cfg["Q"], cfg["H"], cfg["R"]
+    # templates are shared by all ranks (same seed); images differ per rank
+    grid, deltas, tmpl, _, _ = make_workload_torch(**{**cfg, "N_A": 1}, seed=1000, device=dev)
+    _, _, _, imgs, truth = make_workload_torch(**cfg, seed=2000 + rank, device=dev)
+    T = deltas.shape[0]
+    torch.cuda.synchronize()
+
+    # precompute (not in the step): radial-SVD principal vectors
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ws = torch.empty(P.build_workspace_bytes(R, Q, N_B), dtype=torch.uint8, device=dev)
+    P.build_radial_svd(grid.w, tmpl, H, workspace=ws)  # warm
+    e0.record()
+    U, eig = P.build_radial_svd(grid.w, tmpl, H, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    precompute_ms = e0.elapsed_time(e1)
+
+    cA = torch.empty((N_A * T, H, Q // 2, 2), dtype=torch.float32, device=dev)
+    cB = torch.empty((N_B, H, Q // 2, 2), dtype=torch.float32, device=dev)
+    best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
+    arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, args.warmup
+    ev_a0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_a1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_c0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+
+    def step(i=None):
+        if i is not None:
+            ev_c0[i].record(stream)
+        P.compress(grid.k, grid.w, U, imgs, deltas=deltas, out=cA)
+        P.compress(grid.k, grid.w, U, tmpl, out=cB)
+        if i is not None:
+            ev_a0[i].record(stream)
+        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None))
+        if i is not None:
+            ev_a1[i].record(stream)
+
+    for _ in range(W):
+        step()
+    P.status()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(K):
+        step(i)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    align_ms = [ev_a0[i].elapsed_time(ev_a1[i]) for i in range(K)]
+    compress_ms = [ev_c0[i].elapsed_time(ev_a0[i]) for i in range(K)]
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    P.status()
+
+    pairs = N_A * T * N_B
+    scores_step = pairs * Q
+    ms_per_step = elapsed_ms / K
+    value = world * scores_step * K / (elapsed_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ----
+    imgs_h = imgs.cpu().pin_memory()
+    tmpl_h = tmpl.cpu().pin_memory()
+    best_h = torch.empty(best.shape, dtype=best.dtype).pin_memory()
+    arg_h = torch.empty(arg.shape, dtype=arg.dtype).pin_memory()
+    imgs_d = torch.empty_like(imgs)
+    tmpl_d = torch.empty_like(tmpl)
+
+    def e2e_step():
+        imgs_d.copy_(imgs_h, non_blocking=True)
+        tmpl_d.copy_(tmpl_h, non_blocking=True)
+        P.compress(grid.k, grid.w, U, imgs_d, deltas=deltas, out=cA)
+        P.compress(grid.k, grid.w, U, tmpl_d, out=cB)
+        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None))
+        best_h.copy_(best, non_blocking=True)
+        arg_h.copy_(arg, non_blocking=True)
+
+    K2 = max(3, min(K, 10))
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(K2):
+        e2e_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / K2
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = imgs.numel() * 8 + tmpl.numel() * 8
+    d2h = best.numel() * 4 + arg.numel() * 4
+
+    # ---- roofline of the dominant kernel (fused contraction + FFT + reduce) ----
+    align_avg_ms = sum(align_ms) / K
+    flops = pairs * _alg_flops_per_pair(H, Q)
+    achieved = flops / (align_avg_ms / 1e3) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
+    roofline = {"bound": "alu", "kernel": "fused_align_kernel<128,12>", "achieved": round(achieved, 2),
+                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": _load_traffic("fused_align_kernel<128,12>@throughput"),
+                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
+                "align_ms": round(align_avg_ms, 3), "compress_ms": round(sum(compress_ms) / K, 3)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
+        "config": {"workload": _workload_desc(cfg), "N_A_per_gpu": N_A, "N_B": N_B, "T": T, "Q": Q, "R": R, "H": H,
+                   "N": cfg["N"], "snr": cfg["snr"], "parallelism": f"dp{world} (images sharded, templates replicated)",
+                   "l2": "inputs larger than L2 (polar images %.2f GB/GPU), no flush" % (imgs.numel() * 8 / 1e9),
+                   "precompute_ms": round(precompute_ms, 3)},
+        "roofline": roofline,
+        "e2e": {"value": world * scores_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 3 * K,
+        "clocks": clk,
+    }
+
+    # ---- cpu baseline: the FP64 oracle on host cores, bounded sample ----
+    if want_cpu:
+        import oracle as O
+
+        Un = U.cpu().numpy()
+        b_c = O.compress(tmpl.cpu().numpy().astype(np.complex128), Un, grid.w)
+        pool, ncores = _oracle_pool(grid.k, grid.w, deltas, Un, b_c)
+        try:
+            n_s = max(ncores, int(args.cpu_images))
+            sel = np.arange(n_s)
+            A = imgs[:n_s].cpu().numpy().astype(np.complex128)
+            _time_oracle(pool, A[:ncores], 1)  # warm the workers
+            wall, res = _time_oracle(pool, A, max(1, n_s // ncores))
+        finally:
+            pool.close()
+            pool.join()
+        rb = np.concatenate([r[0] for r in res])
+        ra = np.concatenate([r[1] for r in res])
+        gb = best[:n_s].cpu().numpy()
+        ga = arg[:n_s].cpu().numpy()
+        scale = np.maximum(np.abs(rb), 1e-30)
+        out["cpu_baseline"] = {"value": n_s * T * N_B * Q / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                               "sample": f"{n_s} images x {T} translations x {N_B} templates x {Q} rotations "
+                                         f"(FP64 numpy oracle, one spawned process per core; templates "
+                                         f"compressed before timing), {wall:.1f} s"}
+        out["error"] = {"vs": "FP64 oracle on the cpu_baseline sample", "pairs": int(n_s * N_B),
+                        "best_max_rel": float(np.max(np.abs(gb - rb) / scale)),
+                        "argmax_agree": float(np.mean(ga == ra))}
+        del sel
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, same workload, bounded sample per step."""
+    import numpy as np
+
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from synthetic import CONFIGS, make_workload
+
+    cfg = dict(CONFIGS[args.config])
+    wl = make_workload(**{**cfg, "N_A": _cores()}, seed=2000)
+    g = wl.grid
+    T = wl.deltas.shape[0]
+    U, _ = O.principal_vectors(O.radial_kernel(wl.templates.astype(np.complex64).astype(np.complex128), g.w),
+                               cfg["H"])
+    b_c = O.compress(wl.templates.astype(np.complex64).astype(np.complex128), U, g.w)
+    A = wl.images.astype(np.complex64).astype(np.complex128)
+    pool, ncores = _oracle_pool(g.k, g.w, wl.deltas, U, b_c)
+    try:
+        for _ in range(args.warmup):
+            _time_oracle(pool, A, 1)
+        walls = []
+        for _ in range(args.steps):
+            w_, _ = _time_oracle(pool, A, 1)
+            walls.append(w_)
+    finally:
+        pool.close()
+        pool.join()
+    n_s = A.shape[0]
+    per_step = n_s * T * cfg["N_B"] * cfg["Q"]
+    total = sum(walls)
+    value = per_step * len(walls) / total
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(walls), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
+        "impl": "reference",
+        "config": {"workload": _workload_desc(cfg), "N_A_per_gpu": cfg["N_A"], "N_B": cfg["N_B"], "T": T,
+                   "Q": cfg["Q"], "R": cfg["R"], "H": cfg["H"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": f"each step: {n_s} images x {T} translations x {cfg['N_B']} templates x "
+                                   f"{cfg['Q']} rotations, one image per spawned process (FP64 numpy oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="throughput")
+    ap.add_argument("--n-images", type=int, default=0, help="override images per GPU (smaller runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-images", type=int, default=64, help="images in the cpu_baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

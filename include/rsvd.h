@@ -1,0 +1,162 @@
+/*
+ * rsvd.h -- C ABI of the GB300 (sm_103a) radial-SVD image-alignment library.
+ *
+ * The library scores N_A images against N_B templates over Q rotations and
+ * T translations with the radial-SVD compression of Rangan, "Radial-
+ * recombination for rigid rotational alignment of images and volumes"
+ * (arXiv 2202.07235). Notation follows the paper: R rings k_r with radial
+ * weights w_r, Q equispaced angles psi_q = 2 pi q / Q, H principal vectors.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Polar samples are complex64 (interleaved float re, im), row-major
+ *   [object][r][q]: sample (r, q) is F_hat(k_r, psi_q). Inputs must be the
+ *   Fourier transforms of real images, i.e. sample (r, q + Q/2) equals the
+ *   conjugate of sample (r, q); the library reads only q < Q/2 and uses this
+ *   symmetry for the rest.
+ * - Q must be a power of two in [16, 1024]; 1 <= R <= 256; 1 <= H <= min(R, 64);
+ *   1 <= T <= 64.
+ * - "dev" pointers are device memory of the current CUDA device, "host"
+ *   pointers are host memory read during the call. The caller allocates and
+ *   owns every buffer; the library allocates no memory.
+ * - stream is a cudaStream_t (NULL = legacy default stream). Every call only
+ *   enqueues work on that stream and returns; host arrays are consumed
+ *   before the call returns. Outputs are valid once the stream reaches the
+ *   work.
+ * - Return value: RSVD_OK or a negative RSVD_E* code (see rsvd_strerror). On
+ *   an argument error nothing is enqueued. Kernels never trap: a device-side
+ *   check that fails records a code in a per-device status word that
+ *   rsvd_status() reports.
+ */
+#ifndef RSVD_H
+#define RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSVD_ABI_VERSION 1
+
+enum rsvd_status_code {
+  RSVD_OK = 0,
+  RSVD_EINVAL = -1,        /* NULL pointer, non-positive or inconsistent size   */
+  RSVD_EUNSUPPORTED = -2,  /* size outside the limits listed above              */
+  RSVD_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed       */
+  RSVD_EDEVICE = -4,       /* a kernel's own bounds check failed (status word)  */
+  RSVD_ETIMEOUT = -5,      /* a bounded device-side wait gave up (status word)  */
+  RSVD_EWORKSPACE = -6,    /* workspace pointer NULL or smaller than required   */
+  RSVD_ENOCONVERGE = -7    /* eigen-solver sweep limit reached (status word)    */
+};
+
+/* Operand precision of the compressed rings. Only RSVD_FP32 is implemented in
+ * this version; the others return RSVD_EUNSUPPORTED. */
+enum rsvd_precision { RSVD_FP32 = 0, RSVD_BF16 = 1, RSVD_FP16 = 2, RSVD_BF16X3 = 3 };
+
+/* RSVD_ABI_VERSION of the loaded library. */
+int rsvd_abi_version(void);
+
+/* Static text for a status code (never NULL). */
+const char* rsvd_strerror(int code);
+
+/* Synchronises `stream`, then returns and clears the status word of the
+ * current device: RSVD_OK, RSVD_EDEVICE, RSVD_ETIMEOUT or RSVD_ENOCONVERGE
+ * (the first failure recorded since the last call), or RSVD_ECUDA if the
+ * synchronisation itself failed. */
+int rsvd_status(void* stream);
+
+/* ------------------------------------------------------------------------
+ * Precompute: ring-ring kernel C and its principal vectors.
+ * Paper section 3.3, eq. (Image_simple_kern): C_{rr'} is proportional to
+ * sum_{q != 0} conj(b(k_r, q)) b(k_r', q) with b the Fourier-Bessel
+ * coefficients of a template; section 3.4, eq. (image_cost_and_kern): C is
+ * the mean over the N_B templates. Here ring r is weighted by sqrt(w_r) and
+ * the constant prefactor is dropped:
+ *   C_{rr'} = (1/N_B) sum_j sum_{q != 0} Re conj(beta_j(r,q)) beta_j(r',q),
+ *   beta_j(r,q) = sqrt(w_r) b_j(k_r,q),  b_j(k_r,q) = (1/Q) sum_psi B_j(k_r,psi) e^{-i q psi}.
+ * Computed in FP64 on the device. Principal vectors (section 3.3) are the
+ * eigenvectors of C by decreasing eigenvalue, each signed so that its
+ * largest-magnitude entry is positive.
+ *
+ *   R, Q       grid size                      w     host double[R] radial weights
+ *   templates  dev complex64 [N_B][R][Q]      N_B   >= 1
+ *   H          number of vectors kept (1..R, <= 64)
+ *   U          dev double [R][H] (row r, column h) -- output
+ *   eig        dev double [R] eigenvalues, decreasing -- output
+ *   workspace  dev, >= rsvd_build_workspace_bytes(R, Q, N_B) bytes, 256-byte aligned
+ * ------------------------------------------------------------------------ */
+size_t rsvd_build_workspace_bytes(int R, int Q, int N_B);
+int rsvd_build_radial_svd(int R, int Q, const double* w, const void* templates, int N_B, int H,
+                          double* U, double* eig, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* ------------------------------------------------------------------------
+ * Compression: translated principal-image-rings in the Fourier-Bessel basis.
+ * Paper section 3.2 ([u^T A](psi_q) = sum_r u_r A(k_r, psi_q) eta_r) and
+ * eq. (image_innerproduct_pm); translations T_delta of section 5
+ * (eq. Image_single_cost_with_translations) act as
+ * (T_delta A)^(k) = A^(k) exp(-i k . delta). For each object n and
+ * translation t:
+ *   A_t(r, psi)  = A_n(k_r, psi) exp(-i k_r (dx_t cos psi + dy_t sin psi))
+ *   a_t(h, psi)  = sum_r U[r][h] sqrt(w_r) A_t(r, psi)
+ *   a_t(h, q)    = (1/Q) sum_psi a_t(h, psi) e^{-2 pi i q psi / Q},  q = 0 .. Q/2
+ *
+ *   k, w       host double[R]: ring radii and radial weights
+ *   U          dev double [R][H] (as written by rsvd_build_radial_svd)
+ *   polar      dev complex64 [N][R][Q]
+ *   deltas     host double [T][2] (dx, dy) in image units ([-1,1]^2 box);
+ *              NULL means T = 1 and delta = 0 (templates)
+ *   out        dev, rsvd_compressed_bytes(N, T, H, Q, precision) bytes, 16-byte aligned
+ *
+ * Layout of `out` for RSVD_FP32: row n*T + t holds H x (Q/2) complex64 values,
+ * element [row][h][s] at offset ((row*H + h)*(Q/2) + s)*8 bytes, where slot
+ * s >= 1 is a_t(h, s) and slot 0 packs the two real coefficients
+ * (Re a_t(h, 0), Re a_t(h, Q/2)).
+ * ------------------------------------------------------------------------ */
+size_t rsvd_compressed_bytes(int N, int T, int H, int Q, int precision);
+int rsvd_compress(int R, int Q, const double* k, const double* w, const double* U, int H,
+                  const void* polar, int N, const double* deltas, int T, int precision, void* out,
+                  void* stream);
+
+/* ------------------------------------------------------------------------
+ * Full score array (small problems). Eq. (image_innerproduct_pm):
+ *   Step 1  X_hat(q) = 2 pi sum_h conj(a_h(q)) b_h(q)
+ *   Step 2  X(gamma_m) = sum_{q=0}^{Q-1} e^{-i q gamma_m} X_hat(q),  gamma_m = 2 pi m / Q
+ * evaluated from the half spectrum (X_hat(Q-q) = conj(X_hat(q)) for real images).
+ *
+ *   cA   dev compressed images, N_A objects x T translations (rsvd_compress)
+ *   cB   dev compressed templates, N_B objects, T = 1
+ *   X    dev float [N_A][T][N_B][Q] -- output; X[n][t][j][m] = X(gamma_m) for
+ *        image n translated by delta_t against template j
+ * ------------------------------------------------------------------------ */
+int rsvd_align_scores(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
+                      int precision, float* X, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Fused best alignment and log-sum-exp (section 2.7: gamma_opt = argmax X;
+ * section 2.6 likelihood marginalised over rotations and translations).
+ * Same X as rsvd_align_scores, never written to memory. For each (n, j):
+ *   best[n][j] = max_{t, m} X[n][t][j][m]
+ *   arg[n][j]  = t*Q + m of that maximum (smallest t*Q+m among equal values)
+ *   lse[n][j]  = log sum_{t, m} exp(inv_sigma2 * X[n][t][j][m])   (if lse != NULL)
+ *
+ *   best dev float [N_A][N_B], arg dev int32 [N_A][N_B], lse dev float [N_A][N_B] or NULL
+ * ------------------------------------------------------------------------ */
+int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
+                    int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
+                    void* stream);
+
+/* Same contract as rsvd_align_best, always on the generic per-pair kernel
+ * (one CTA per (image, template), all T translations, any supported Q and H).
+ * Provided so callers can cross-check the fused kernel. */
+int rsvd_align_best_pairwise(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
+                             int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSVD_H */

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) radial-SVD rotational alignment of images (arXiv 2202.07235).
+
+The compute path is librsvd.so (hand-written CUDA, C ABI in include/rsvd.h);
+this package is the thin Python binding: ``build_radial_svd``, ``compress``,
+``align_scores``, ``align_best``, ``status``.
+"""
+
+from ._native import RSVDError, lib, lib_path  # noqa: F401
+from .api import (  # noqa: F401
+    FP32,
+    align_best,
+    align_scores,
+    build_radial_svd,
+    build_workspace_bytes,
+    compress,
+    compressed_bytes,
+    status,
+)

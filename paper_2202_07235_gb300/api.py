@@ -1,0 +1,121 @@
+"""PyTorch-facing wrappers over the librsvd C ABI (include/rsvd.h).
+
+torch is used only to allocate device memory and to name the current CUDA
+stream; every arithmetic step runs in librsvd's CUDA kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._native import check, lib
+
+FP32 = 0
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return int(t.data_ptr())
+
+
+def _host_f64(x) -> tuple[np.ndarray, ctypes.POINTER]:
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _require_cuda(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def build_workspace_bytes(R: int, Q: int, N_B: int) -> int:
+    return int(lib().rsvd_build_workspace_bytes(R, Q, N_B))
+
+
+def build_radial_svd(w, templates: torch.Tensor, H: int, workspace: torch.Tensor | None = None, stream=None):
+    """Principal vectors of the ring-ring kernel C. templates: complex64 [N_B, R, Q]
+    on the device. Returns (U float64 [R, H], eig float64 [R])."""
+    _require_cuda(templates, torch.complex64, "templates")
+    N_B, R, Q = templates.shape
+    wa, wp = _host_f64(w)
+    if wa.shape != (R,):
+        raise ValueError("w must have length R")
+    dev = templates.device
+    U = torch.empty((R, H), dtype=torch.float64, device=dev)
+    eig = torch.empty((R,), dtype=torch.float64, device=dev)
+    need = build_workspace_bytes(R, Q, N_B)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    check(lib().rsvd_build_radial_svd(R, Q, wp, _ptr(templates), N_B, H, _ptr(U), _ptr(eig), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), _stream(stream)),
+          "rsvd_build_radial_svd")
+    return U, eig
+
+
+def compressed_bytes(N: int, T: int, H: int, Q: int, precision: int = FP32) -> int:
+    return int(lib().rsvd_compressed_bytes(N, T, H, Q, precision))
+
+
+def compress(k, w, U: torch.Tensor, polar: torch.Tensor, deltas=None, precision: int = FP32,
+             out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Compressed rings. polar: complex64 [N, R, Q]; deltas: host (T, 2) or None.
+    Returns float32 [N*T, H, Q/2, 2] (complex slots; slot 0 packs q = 0 and q = Q/2)."""
+    _require_cuda(polar, torch.complex64, "polar")
+    _require_cuda(U, torch.float64, "U")
+    N, R, Q = polar.shape
+    H = U.shape[1]
+    ka, kp = _host_f64(k)
+    wa, wp = _host_f64(w)
+    if deltas is None:
+        T, dp, da = 1, None, None
+    else:
+        da, dp = _host_f64(deltas)
+        T = da.reshape(-1, 2).shape[0]
+    if out is None:
+        out = torch.empty((N * T, H, Q // 2, 2), dtype=torch.float32, device=polar.device)
+    check(lib().rsvd_compress(R, Q, kp, wp, _ptr(U), H, _ptr(polar), N, dp, T, precision, _ptr(out),
+                              _stream(stream)), "rsvd_compress")
+    return out
+
+
+def align_scores(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int,
+                 precision: int = FP32, stream=None) -> torch.Tensor:
+    """Full landscape X float32 [N_A, T, N_B, Q]."""
+    X = torch.empty((N_A, T, N_B, Q), dtype=torch.float32, device=cA.device)
+    check(lib().rsvd_align_scores(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, _ptr(X), _stream(stream)),
+          "rsvd_align_scores")
+    return X
+
+
+def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int,
+               inv_sigma2: float = 1.0, want_lse: bool = False, precision: int = FP32, out=None, stream=None,
+               pairwise: bool = False):
+    """best float32 [N_A, N_B], arg int32 [N_A, N_B] (t*Q+m), lse float32 or None."""
+    dev = cA.device
+    if out is None:
+        best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
+        arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
+        lse = torch.empty((N_A, N_B), dtype=torch.float32, device=dev) if want_lse else None
+    else:
+        best, arg, lse = out
+    fn = lib().rsvd_align_best_pairwise if pairwise else lib().rsvd_align_best
+    check(fn(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, float(inv_sigma2), _ptr(best), _ptr(arg),
+             _ptr(lse) if lse is not None else None, _stream(stream)), "rsvd_align_best")
+    return best, arg, lse
+
+
+def status(stream=None) -> None:
+    """Synchronises the stream and raises if a kernel recorded a device-side failure."""
+    check(lib().rsvd_status(_stream(stream)), "rsvd_status")

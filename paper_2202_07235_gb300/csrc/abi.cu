@@ -1,0 +1,70 @@
+// Library-wide entry points: version, error strings, device status word,
+// buffer-size queries.
+#include <mutex>
+
+#include "rsvd_internal.cuh"
+
+namespace rsvd {
+
+// One status word per device that loads the module (first failure wins;
+// rsvd_status reads and clears it).
+__device__ int g_status_word = 0;
+
+RSVD_HIDDEN int* status_word() {
+  static std::mutex mu;
+  static int* ptrs[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int*>(p);
+  }
+  return ptrs[dev];
+}
+
+}  // namespace rsvd
+
+extern "C" {
+
+int rsvd_abi_version(void) { return RSVD_ABI_VERSION; }
+
+const char* rsvd_strerror(int code) {
+  switch (code) {
+    case RSVD_OK: return "ok";
+    case RSVD_EINVAL: return "invalid argument (NULL pointer or inconsistent size)";
+    case RSVD_EUNSUPPORTED: return "unsupported size or precision";
+    case RSVD_ECUDA: return "CUDA runtime error";
+    case RSVD_EDEVICE: return "device-side bounds check failed";
+    case RSVD_ETIMEOUT: return "device-side wait timed out";
+    case RSVD_EWORKSPACE: return "workspace missing or too small";
+    case RSVD_ENOCONVERGE: return "eigen-solver did not converge";
+    default: return "unknown status code";
+  }
+}
+
+int rsvd_status(void* stream) {
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return RSVD_ECUDA;
+  int* p = rsvd::status_word();
+  if (!p) return RSVD_ECUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RSVD_ECUDA;
+  if (v != 0) {
+    int zero = 0;
+    if (cudaMemcpy(p, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return RSVD_ECUDA;
+  }
+  switch (v) {
+    case rsvd::kDevOk: return RSVD_OK;
+    case rsvd::kDevTimeout: return RSVD_ETIMEOUT;
+    case rsvd::kDevNoConverge: return RSVD_ENOCONVERGE;
+    default: return RSVD_EDEVICE;
+  }
+}
+
+size_t rsvd_compressed_bytes(int N, int T, int H, int Q, int precision) {
+  if (N <= 0 || T <= 0 || H <= 0 || Q <= 0 || precision != RSVD_FP32) return 0;
+  return (size_t)N * (size_t)T * (size_t)H * (size_t)(Q / 2) * 8u;
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// rsvd_build_radial_svd: ring-ring kernel C (FP64) and its principal vectors.
+//
+// Paper section 3.3, eq. (Image_simple_kern) and section 3.4,
+// eq. (image_cost_and_kern):  C_{rr'} = (1/N_B) sum_j sum_{q != 0}
+// Re conj(beta_j(r,q)) beta_j(r',q), beta_j(r,q) = sqrt(w_r) b_j(k_r,q).
+//
+// The q-sum is evaluated without an FFT through Parseval's identity on each
+// ring, sum_{q} conj(b(r,q)) b(r',q) = (1/Q) sum_psi conj(B(r,psi)) B(r',psi), minus the
+// q = 0 term b(r,0) = (1/Q) sum_psi B(r,psi) (the ring mean). For the transform of a
+// real image the psi and psi+pi samples are conjugate, so with M = Q/2:
+//   G_{rr'}   = sum_j sum_{psi<M} Re conj(B_j(r,psi)) B_j(r',psi)
+//   m_j(r)    = (2/Q) sum_{psi<M} Re B_j(r,psi)
+//   C_{rr'}   = sqrt(w_r w_r') / N_B * [ (2/Q) G_{rr'} - sum_j m_j(r) m_j(r') ].
+// kernel_partial: CTA (slice, tile) accumulates a 64x64 tile of C over a slice
+// of templates (FP64, 4x4 register block per thread) into the workspace;
+// kernel_reduce: sums the slices. jacobi_eig: cyclic Jacobi with the
+// round-robin (tournament) ordering on one CTA, FP64, then sorting,
+// sign-fixing and writing U and the eigenvalues.
+#include <math.h>
+
+#include "rsvd_internal.cuh"
+
+namespace rsvd {
+namespace {
+
+constexpr int kTile = 64;       // C tile edge
+constexpr int kPsiChunk = 32;   // angles staged per step
+constexpr int kThreads = 256;   // 16 x 16 threads, 4 x 4 entries each
+constexpr int kMaxSlices = 304;
+constexpr int kJacobiThreads = 1024;
+constexpr int kMaxSweeps = 40;
+
+struct BuildPlan {
+  int tiles1d, ntiles, nslices;
+  size_t off_partial, off_C, off_A, off_V, total;
+};
+
+BuildPlan make_plan(int R, int N_B) {
+  BuildPlan pl{};
+  pl.tiles1d = (R + kTile - 1) / kTile;
+  pl.ntiles = pl.tiles1d * pl.tiles1d;
+  int ns = kMaxSlices / pl.ntiles;
+  if (ns < 1) ns = 1;
+  if (ns > N_B) ns = N_B;
+  pl.nslices = ns;
+  const size_t rr = (size_t)R * R * sizeof(double);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  pl.off_partial = 0;
+  pl.off_C = up((size_t)ns * rr);
+  pl.off_A = pl.off_C + up(rr);
+  pl.off_V = pl.off_A + up(rr);
+  pl.total = pl.off_V + up(rr);
+  return pl;
+}
+
+__global__ void __launch_bounds__(kThreads) kernel_partial(const float2* __restrict__ B, int N_B, int R, int Q,
+                                                           int tiles1d, int nslices, double* __restrict__ partial) {
+  __shared__ float2 sr[kTile][kPsiChunk + 1];
+  __shared__ float2 sc[kTile][kPsiChunk + 1];
+  const int slice = blockIdx.x, tile = blockIdx.y;
+  const int tr = tile / tiles1d, tc = tile % tiles1d;
+  const int r0 = tr * kTile, c0 = tc * kTile;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int M = Q / 2;
+  const int j_begin = (int)((long long)N_B * slice / nslices);
+  const int j_end = (int)((long long)N_B * (slice + 1) / nslices);
+  const double scale_g = 2.0 / (double)Q;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+  for (int j = j_begin; j < j_end; ++j) {
+    const float2* Bj = B + (size_t)j * R * Q;
+    double g[4][4];
+    double mr[4] = {0, 0, 0, 0}, mc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) g[a][b] = 0.0;
+    for (int p0 = 0; p0 < M; p0 += kPsiChunk) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < kTile * kPsiChunk; i += kThreads) {
+        const int rr = i / kPsiChunk, pp = i % kPsiChunk;
+        const int psi = p0 + pp;
+        const bool okp = psi < M;
+        sr[rr][pp] = (okp && r0 + rr < R) ? Bj[(size_t)(r0 + rr) * Q + psi] : make_float2(0.f, 0.f);
+        sc[rr][pp] = (okp && c0 + rr < R) ? Bj[(size_t)(c0 + rr) * Q + psi] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int pp = 0; pp < kPsiChunk; ++pp) {
+        double xr[4], xi[4], yr[4], yi[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float2 u = sr[ty * 4 + a][pp];
+          const float2 v = sc[tx * 4 + a][pp];
+          xr[a] = u.x;
+          xi[a] = u.y;
+          yr[a] = v.x;
+          yi[a] = v.y;
+          mr[a] += xr[a];
+          mc[a] += yr[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) g[a][b] = fma(xr[a], yr[b], fma(xi[a], yi[b], g[a][b]));
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        acc[a][b] += scale_g * g[a][b] - (scale_g * mr[a]) * (scale_g * mc[b]);
+  }
+  double* out = partial + (size_t)slice * R * R;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = r0 + ty * 4 + a;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (r < R && c < R) out[(size_t)r * R + c] = acc[a][b];
+    }
+  }
+}
+
+struct ReduceParams {
+  const double* partial;
+  double* C;
+  int R, nslices, N_B;
+  double sw[kMaxR];
+};
+
+__global__ void kernel_reduce(const __grid_constant__ ReduceParams p) {
+  const int RR = p.R * p.R;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RR; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < p.nslices; ++k) s += p.partial[(size_t)k * RR + i];
+    const int r = i / p.R, c = i % p.R;
+    p.C[i] = s * p.sw[r] * p.sw[c] / (double)p.N_B;
+  }
+}
+
+// Position of element i in round k of the round-robin schedule over n (even)
+// indices: index 0 stays, the others rotate.
+__device__ __forceinline__ int rr_member(int pos, int k, int n) { return pos == 0 ? 0 : ((pos - 1 + k) % (n - 1)) + 1; }
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_eig(const double* __restrict__ C, double* A, double* V, int R,
+                                                              int H, double* __restrict__ U, double* __restrict__ eig,
+                                                              int use_smem, int* status) {
+  extern __shared__ __align__(16) double jsm[];
+  __shared__ double cs_c[kMaxR / 2 + 1], cs_s[kMaxR / 2 + 1];
+  __shared__ int pr_p[kMaxR / 2 + 1], pr_q[kMaxR / 2 + 1];
+  __shared__ int rotated;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int n = (R % 2) ? R + 1 : R;  // padded to even; index R (if any) is a dummy
+  if (use_smem) {
+    A = jsm;
+    V = jsm + (size_t)R * R;
+  }
+  for (int i = tid; i < R * R; i += nth) {
+    const int r = i / R, c = i % R;
+    A[i] = 0.5 * (C[i] + C[(size_t)c * R + r]);  // exact symmetry
+    V[i] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int npairs = n / 2;
+  __shared__ double anorm;
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < R; ++i) m = fmax(m, fabs(A[(size_t)i * R + i]));
+    anorm = m;
+  }
+  __syncthreads();
+  // rotate while |a_pq| exceeds both a relative (to sqrt(a_pp a_qq)) and an
+  // absolute (to the largest diagonal entry) rounding-level threshold
+  const double abs_floor = 1e-17 * anorm;
+  int sweep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int k = 0; k < n - 1; ++k) {
+      // rotation parameters (Golub & Van Loan, symmetric Schur 2x2)
+      for (int i = tid; i < npairs; i += nth) {
+        int pp = rr_member(i, k, n), qq = rr_member(n - 1 - i, k, n);
+        if (pp > qq) {
+          const int tmp = pp;
+          pp = qq;
+          qq = tmp;
+        }
+        double c = 1.0, s = 0.0;
+        if (qq < R) {
+          const double apq = A[(size_t)pp * R + qq];
+          const double app = A[(size_t)pp * R + pp], aqq = A[(size_t)qq * R + qq];
+          if (fabs(apq) > fmax(1e-15 * sqrt(fabs(app * aqq)), abs_floor) && apq != 0.0) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            rotated = 1;
+          }
+        }
+        cs_c[i] = c;
+        cs_s[i] = s;
+        pr_p[i] = pp;
+        pr_q[i] = qq;
+      }
+      __syncthreads();
+      // columns of A and V: A <- A J, V <- V J
+      for (int idx = tid; idx < npairs * R; idx += nth) {
+        const int i = idx / R, r = idx % R;
+        const int pp = pr_p[i], qq = pr_q[i];
+        if (qq >= R || cs_s[i] == 0.0) continue;
+        const double c = cs_c[i], s = cs_s[i];
+        const double ap = A[(size_t)r * R + pp], aq = A[(size_t)r * R + qq];
+        A[(size_t)r * R + pp] = c * ap - s * aq;
+        A[(size_t)r * R + qq] = s * ap + c * aq;
+        const double vp = V[(size_t)r * R + pp], vq = V[(size_t)r * R + qq];
+        V[(size_t)r * R + pp] = c * vp - s * vq;
+        V[(size_t)r * R + qq] = s * vp + c * vq;
+      }
+      __syncthreads();
+      // rows of A: A <- J^T A
+      for (int idx = tid; idx < npairs * R; idx += nth) {
+        const int i = idx / R, cidx = idx % R;
+        const int pp = pr_p[i], qq = pr_q[i];
+        if (qq >= R || cs_s[i] == 0.0) continue;
+        const double c = cs_c[i], s = cs_s[i];
+        const double ap = A[(size_t)pp * R + cidx], aq = A[(size_t)qq * R + cidx];
+        A[(size_t)pp * R + cidx] = c * ap - s * aq;
+        A[(size_t)qq * R + cidx] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (sweep >= kMaxSweeps && tid == 0) record(status, kDevNoConverge);
+  // sort by decreasing eigenvalue (stable on index), fix signs, write out
+  for (int i = tid; i < R; i += nth) {
+    const double li = A[(size_t)i * R + i];
+    int rank = 0;
+    for (int j = 0; j < R; ++j) {
+      const double lj = A[(size_t)j * R + j];
+      if (lj > li || (lj == li && j < i)) ++rank;
+    }
+    eig[rank] = li;
+    if (rank < H) {
+      int imax = 0;
+      double vmax = -1.0;
+      for (int r = 0; r < R; ++r) {
+        const double v = fabs(V[(size_t)r * R + i]);
+        if (v > vmax) {
+          vmax = v;
+          imax = r;
+        }
+      }
+      const double sg = V[(size_t)imax * R + i] < 0.0 ? -1.0 : 1.0;
+      for (int r = 0; r < R; ++r) U[(size_t)r * H + rank] = sg * V[(size_t)r * R + i];
+    }
+  }
+}
+
+}  // namespace
+}  // namespace rsvd
+
+extern "C" size_t rsvd_build_workspace_bytes(int R, int Q, int N_B) {
+  if (R <= 0 || R > rsvd::kMaxR || Q <= 0 || N_B <= 0) return 0;
+  return rsvd::make_plan(R, N_B).total;
+}
+
+extern "C" int rsvd_build_radial_svd(int R, int Q, const double* w, const void* templates, int N_B, int H, double* U,
+                                     double* eig, void* workspace, size_t workspace_bytes, void* stream) {
+  using namespace rsvd;
+  int rc = check_grid(R, Q, H);
+  if (rc != RSVD_OK) return rc;
+  if (!w || !templates || !U || !eig || N_B <= 0) return RSVD_EINVAL;
+  if (((uintptr_t)templates & 7u) || ((uintptr_t)U & 7u) || ((uintptr_t)eig & 7u)) return RSVD_EINVAL;
+  const BuildPlan pl = make_plan(R, N_B);
+  if (!workspace || workspace_bytes < pl.total || ((uintptr_t)workspace & 255u)) return RSVD_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  double* partial = reinterpret_cast<double*>(ws + pl.off_partial);
+  double* C = reinterpret_cast<double*>(ws + pl.off_C);
+  double* A = reinterpret_cast<double*>(ws + pl.off_A);
+  double* V = reinterpret_cast<double*>(ws + pl.off_V);
+
+  dim3 grid(pl.nslices, pl.ntiles);
+  kernel_partial<<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.tiles1d, pl.nslices,
+                                            partial);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  ReduceParams rp{};
+  rp.partial = partial;
+  rp.C = C;
+  rp.R = R;
+  rp.nslices = pl.nslices;
+  rp.N_B = N_B;
+  for (int r = 0; r < R; ++r) {
+    if (!(w[r] >= 0.0)) return RSVD_EINVAL;
+    rp.sw[r] = sqrt(w[r]);
+  }
+  kernel_reduce<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  const size_t need = (size_t)2 * R * R * sizeof(double);
+  const int use_smem = need <= 160 * 1024 ? 1 : 0;
+  const size_t smem = use_smem ? need : 0;
+  if (use_smem &&
+      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RSVD_ECUDA;
+  jacobi_eig<<<1, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
+  return launch_status();
+}

@@ -106,16 +106,21 @@ def blobs_polar_ft(grid: PolarGrid, blobs: Blobs, rotation: np.ndarray | None = 
         c = np.stack([cr * c[..., 0] - sr * c[..., 1], sr * c[..., 0] + cr * c[..., 1]], axis=-1)
     if shift is not None:
         c = c + shift[:, None, :]
-    kx = grid.k[:, None] * np.cos(grid.psi)[None, :]  # [R, Q]
-    ky = grid.k[:, None] * np.sin(grid.psi)[None, :]
+    # angles psi < pi are evaluated; the sample at psi + pi of a real image is
+    # the conjugate (F(-k) = conj F(k)), so the pairing holds bit-exactly
+    half = grid.Q // 2 if grid.Q % 2 == 0 else grid.Q
+    kx = grid.k[:, None] * np.cos(grid.psi[:half])[None, :]  # [R, half]
+    ky = grid.k[:, None] * np.sin(grid.psi[:half])[None, :]
     k2 = (grid.k ** 2)[:, None]
-    out = np.zeros((n, grid.R, grid.Q), dtype=np.complex128)
+    out = np.zeros((n, grid.R, half), dtype=np.complex128)
     for b in range(c.shape[1]):
         s2 = (blobs.widths[:, b] ** 2)[:, None, None]
         amp = (blobs.amps[:, b] * 2.0 * math.pi)[:, None, None] * s2 * np.exp(-0.5 * s2 * k2[None])
         ph = kx[None] * c[:, b, 0][:, None, None] + ky[None] * c[:, b, 1][:, None, None]
         out += amp * np.exp(-1j * ph)
-    return out
+    if half == grid.Q:
+        return out
+    return np.concatenate([out, np.conj(out)], axis=-1)
 
 
 def polar_norm2(grid: PolarGrid, F: np.ndarray) -> np.ndarray:
@@ -218,21 +223,23 @@ def make_workload_torch(N: int, R: int, Q: int, N_B: int, N_A: int, snr: float |
     amp = 0.5 + 0.5 * u(N_B, nb)
     kk = torch.as_tensor(grid.k, device=device, dtype=f64)
     ps = torch.as_tensor(grid.psi, device=device, dtype=f64)
-    kx = kk[:, None] * torch.cos(ps)[None, :]
-    ky = kk[:, None] * torch.sin(ps)[None, :]
+    half = Q // 2
+    kx = kk[:, None] * torch.cos(ps[:half])[None, :]
+    ky = kk[:, None] * torch.sin(ps[:half])[None, :]
     k2 = (kk ** 2)[:, None]
     wq = torch.as_tensor(grid.w, device=device, dtype=f64)
 
-    def ft(c, s, a):  # c [n,B,2], s [n,B], a [n,B] -> complex128 [n,R,Q]
-        out = torch.zeros((c.shape[0], R, Q), device=device, dtype=torch.complex128)
+    def ft(c, s, a):  # c [n,B,2], s [n,B], a [n,B] -> complex128 [n,R,Q], psi+pi = conjugate
+        out = torch.zeros((c.shape[0], R, half), device=device, dtype=torch.complex128)
         for b in range(c.shape[1]):
             s2 = (s[:, b] ** 2)[:, None, None]
             mag = (a[:, b] * 2.0 * math.pi)[:, None, None] * s2 * torch.exp(-0.5 * s2 * k2[None])
             ph = kx[None] * c[:, b, 0][:, None, None] + ky[None] * c[:, b, 1][:, None, None]
             out += torch.polar(mag, -ph)
-        return out
+        return torch.cat([out, torch.conj(out)], dim=-1)
 
     templates = torch.empty((N_B, R, Q), device=device, dtype=torch.complex64)
+    half = Q // 2
     for i in range(0, N_B, chunk):
         templates[i:i + chunk] = ft(cen[i:i + chunk], wid[i:i + chunk], amp[i:i + chunk]).to(torch.complex64)
     j0 = torch.randint(0, N_B, (N_A,), generator=gen, device=device)

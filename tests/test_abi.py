@@ -1,0 +1,95 @@
+"""The C-ABI library builds, loads and exports every symbol include/rsvd.h
+declares; argument validation answers without touching a GPU."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2202_07235_gb300 import build as B
+
+    B.build()
+    h = ctypes.CDLL(B.LIB)
+    return h
+
+
+def _declared():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\**\s+\**(rsvd_[a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("rsvd_build_radial_svd", "rsvd_compress", "rsvd_align_scores", "rsvd_align_best", "rsvd_status",
+                 "rsvd_strerror", "rsvd_compressed_bytes", "rsvd_build_workspace_bytes"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_2202_07235_gb300._native import SIGNATURES
+
+    assert set(_declared()) <= set(SIGNATURES)
+
+
+def test_version_and_error_strings(lib):
+    lib.rsvd_abi_version.restype = ctypes.c_int
+    assert lib.rsvd_abi_version() == 1
+    lib.rsvd_strerror.restype = ctypes.c_char_p
+    lib.rsvd_strerror.argtypes = [ctypes.c_int]
+    for code in range(0, -8, -1):
+        s = lib.rsvd_strerror(code).decode()
+        assert s and s != "unknown status code"
+    assert lib.rsvd_strerror(-99).decode() == "unknown status code"
+
+
+def test_size_queries(lib):
+    lib.rsvd_compressed_bytes.restype = ctypes.c_size_t
+    lib.rsvd_compressed_bytes.argtypes = [ctypes.c_int] * 5
+    assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 0) == 8192 * 9 * 12 * 128 * 8
+    assert lib.rsvd_compressed_bytes(8, 1, 12, 256, 2) == 0  # precision not implemented
+    lib.rsvd_build_workspace_bytes.restype = ctypes.c_size_t
+    lib.rsvd_build_workspace_bytes.argtypes = [ctypes.c_int] * 3
+    assert lib.rsvd_build_workspace_bytes(64, 256, 1024) >= 3 * 64 * 64 * 8
+    assert lib.rsvd_build_workspace_bytes(0, 256, 1024) == 0
+
+
+def test_argument_errors_return_codes_without_a_gpu(lib):
+    from paper_2202_07235_gb300._native import SIGNATURES
+
+    f = lib.rsvd_align_best
+    f.restype, f.argtypes = SIGNATURES["rsvd_align_best"]
+    one = ctypes.c_void_p(16)
+    # NULL operands
+    assert f(None, 1, 1, one, 1, 8, 256, 0, 1.0, one, one, None, None) == -1
+    # Q not a power of two / precision not implemented / H too large
+    assert f(one, 1, 1, one, 1, 8, 100, 0, 1.0, one, one, None, None) == -2
+    assert f(one, 1, 1, one, 1, 8, 256, 3, 1.0, one, one, None, None) == -2
+    assert f(one, 1, 1, one, 1, 65, 256, 0, 1.0, one, one, None, None) == -2
+    # log-sum-exp requested with a non-positive scale
+    assert f(one, 1, 1, one, 1, 8, 256, 0, 0.0, one, one, one, None) == -1
+    g = lib.rsvd_compress
+    g.restype, g.argtypes = SIGNATURES["rsvd_compress"]
+    k = (ctypes.c_double * 4)(1, 2, 3, 4)
+    assert g(4, 16, k, k, one, 5, one, 1, None, 1, 0, one, None) == -1  # H > R
+    assert g(4, 16, k, k, one, 2, one, 1, None, 3, 0, one, None) == -1  # deltas NULL but T != 1
+    assert g(4, 48, k, k, one, 2, one, 1, None, 1, 0, one, None) == -2  # Q not a power of two
+    h = lib.rsvd_build_radial_svd
+    h.restype, h.argtypes = SIGNATURES["rsvd_build_radial_svd"]
+    assert h(4, 16, ctypes.cast(k, ctypes.POINTER(ctypes.c_double)), one, 3, 2, one, one, None, 0, None) == -6
