@@ -190,7 +190,6 @@ def run_ours(args):
     if args.n_images:
         cfg["N_A"] = args.n_images
 
-    # the oracle pool is started before the first GPU call (spawned workers)
     want_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     torch.cuda.set_device(local)
@@ -357,10 +356,13 @@ def run_ours(args):
         b_c = O.compress(tmpl.cpu().numpy().astype(np.complex128), Un, grid.w)
         pool, ncores = _oracle_pool(grid.k, grid.w, deltas, Un, b_c)
         try:
-            n_s = max(ncores, int(args.cpu_images))
-            sel = np.arange(n_s)
+            A0 = imgs[:ncores].cpu().numpy().astype(np.complex128)
+            _time_oracle(pool, A0, 1)  # warm the workers
+            w0, _ = _time_oracle(pool, A0, 1)
+            # sample sized to about args.cpu_seconds of wall time on all cores
+            n_s = int(args.cpu_images) or int(max(1, args.cpu_seconds / max(w0, 1e-3)) * ncores)
+            n_s = max(ncores, min(N_A, n_s))
             A = imgs[:n_s].cpu().numpy().astype(np.complex128)
-            _time_oracle(pool, A[:ncores], 1)  # warm the workers
             wall, res = _time_oracle(pool, A, max(1, n_s // ncores))
         finally:
             pool.close()
@@ -373,11 +375,10 @@ def run_ours(args):
         out["cpu_baseline"] = {"value": n_s * T * N_B * Q / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
                                "sample": f"{n_s} images x {T} translations x {N_B} templates x {Q} rotations "
                                          f"(FP64 numpy oracle, one spawned process per core; templates "
-                                         f"compressed before timing), {wall:.1f} s"}
+                                         f"compressed before timing), {wall:.1f} s wall"}
         out["error"] = {"vs": "FP64 oracle on the cpu_baseline sample", "pairs": int(n_s * N_B),
                         "best_max_rel": float(np.max(np.abs(gb - rb) / scale)),
                         "argmax_agree": float(np.mean(ga == ra))}
-        del sel
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -443,7 +444,8 @@ def main():
     ap.add_argument("--config", default="throughput")
     ap.add_argument("--n-images", type=int, default=0, help="override images per GPU (smaller runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-images", type=int, default=64, help="images in the cpu_baseline sample")
+    ap.add_argument("--cpu-images", type=int, default=0, help="images in the cpu_baseline sample (0 = auto)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target wall time of the cpu_baseline sample")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
