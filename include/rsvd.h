@@ -92,6 +92,27 @@ int rsvd_build_radial_svd(int R, int Q, const double* w, const void* templates, 
                           double* U, double* eig, void* workspace, size_t workspace_bytes,
                           void* stream);
 
+/* Allocation-free form of rsvd_build_radial_svd (the paper has no
+ * counterpart; it is a memory-management variant of the call above).
+ * For callers that cannot allocate device memory: code that receives only
+ * raw pointers (a plugin or callback with no allocator of its own) and
+ * services that fix their device footprint at start-up. Instead of a caller
+ * workspace it uses a fixed 1 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits; that bounds the
+ * grid to R <= 181 rings (larger R returns RSVD_EUNSUPPORTED). It allocates
+ * nothing: no cudaMalloc, no cudaFree.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) once; make that first call before any stream
+ *   capture on that device.
+ * - Every call uses the same array and it keeps the last call's contents:
+ *   calls that overlap on the GPU (other streams, other host threads on the
+ *   same device) race; serialise them.
+ * Arguments and results are those of rsvd_build_radial_svd without the
+ * workspace; results agree with it to rounding (the partial sums over
+ * templates are grouped differently). */
+int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, const void* templates, int N_B, int H,
+                                  double* U, double* eig, void* stream);
+
 /* ------------------------------------------------------------------------
  * Compression: translated principal-image-rings in the Fourier-Bessel basis.
  * Paper section 3.2 ([u^T A](psi_q) = sum_r u_r A(k_r, psi_q) eta_r) and

@@ -11,6 +11,7 @@ from .api import (  # noqa: F401
     align_best,
     align_scores,
     build_radial_svd,
+    build_radial_svd_noalloc,
     build_workspace_bytes,
     compress,
     compressed_bytes,

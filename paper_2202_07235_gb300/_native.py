@@ -27,6 +27,8 @@ SIGNATURES = {
     "rsvd_build_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
     "rsvd_build_radial_svd": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                       c_size_t, c_void_p]),
+    "rsvd_build_radial_svd_noalloc": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_int, c_void_p, c_void_p,
+                                              c_void_p]),
     "rsvd_compressed_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "rsvd_compress": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_void_p, c_int, c_double_p,
                               c_int, c_int, c_void_p, c_void_p]),

@@ -64,6 +64,22 @@ def build_radial_svd(w, templates: torch.Tensor, H: int, workspace: torch.Tensor
     return U, eig
 
 
+def build_radial_svd_noalloc(w, templates: torch.Tensor, H: int, stream=None):
+    """Same results as build_radial_svd, for callers that cannot allocate scratch
+    device memory: the library's own fixed 1 MiB device array is used instead of
+    a workspace (R <= 181). Calls that overlap on the GPU race on that array."""
+    _require_cuda(templates, torch.complex64, "templates")
+    N_B, R, Q = templates.shape
+    wa, wp = _host_f64(w)
+    if wa.shape != (R,):
+        raise ValueError("w must have length R")
+    U = torch.empty((R, H), dtype=torch.float64, device=templates.device)
+    eig = torch.empty((R,), dtype=torch.float64, device=templates.device)
+    check(lib().rsvd_build_radial_svd_noalloc(R, Q, wp, _ptr(templates), N_B, H, _ptr(U), _ptr(eig), _stream(stream)),
+          "rsvd_build_radial_svd_noalloc")
+    return U, eig
+
+
 def compressed_bytes(N: int, T: int, H: int, Q: int, precision: int = FP32) -> int:
     return int(lib().rsvd_compressed_bytes(N, T, H, Q, precision))
 

@@ -18,6 +18,8 @@
 // sign-fixing and writing U and the eigenvalues.
 #include <math.h>
 
+#include <mutex>
+
 #include "rsvd_internal.cuh"
 
 namespace rsvd {
@@ -302,6 +304,115 @@ extern "C" int rsvd_build_radial_svd(int R, int Q, const double* w, const void* 
     if (!(w[r] >= 0.0)) return RSVD_EINVAL;
     rp.sw[r] = sqrt(w[r]);
   }
+  kernel_reduce<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  const size_t need = (size_t)2 * R * R * sizeof(double);
+  const int use_smem = need <= 160 * 1024 ? 1 : 0;
+  const size_t smem = use_smem ? need : 0;
+  if (use_smem &&
+      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RSVD_ECUDA;
+  jacobi_eig<<<1, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
+  return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of rsvd_build_radial_svd.
+//
+// Some callers cannot allocate device memory: a host application that hands
+// this library raw pointers from inside a plugin or callback has no allocator
+// of its own to call, and a service that fixes its device footprint at start-up
+// must not grow it (or fragment a caching allocator) when the principal
+// vectors are rebuilt. For them the scratch of the build (per-slice partial
+// sums of C, C itself and the two Jacobi matrices) lives in a fixed
+// file-scope device array that every GPU loading the library holds until the
+// process exits. The array keeps the last call's contents; every word a call
+// reads is first written by that same call, so nothing needs clearing. All
+// calls share it: calls that overlap on the GPU (different streams, or
+// different host threads on one device) race and must be serialised by the
+// caller.
+// ---------------------------------------------------------------------------
+namespace rsvd {
+namespace {
+
+// 1 MiB: enough for the four R x R FP64 matrices of the build up to R = 181
+// (fewer template slices are used than in the workspace entry point).
+constexpr size_t kStaticScratchBytes = (size_t)1 << 20;
+static __device__ __align__(256) unsigned char g_build_scratch[kStaticScratchBytes];
+
+BuildPlan make_plan_capped(int R, int N_B, size_t cap) {
+  BuildPlan pl{};
+  pl.tiles1d = (R + kTile - 1) / kTile;
+  pl.ntiles = pl.tiles1d * pl.tiles1d;
+  const size_t rr = (size_t)R * R * sizeof(double);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  int ns = kMaxSlices / pl.ntiles;
+  if (ns < 1) ns = 1;
+  if (ns > N_B) ns = N_B;
+  const size_t fixed = 3 * up(rr);
+  while (ns > 1 && up((size_t)ns * rr) + fixed > cap) --ns;
+  pl.nslices = ns;
+  pl.off_partial = 0;
+  pl.off_C = up((size_t)ns * rr);
+  pl.off_A = pl.off_C + up(rr);
+  pl.off_V = pl.off_A + up(rr);
+  pl.total = pl.off_V + up(rr);
+  return pl;
+}
+
+// Device address of g_build_scratch on the current device, looked up once per
+// device (the host-side name of a __device__ array is only a stand-in).
+int static_scratch(void** out) {
+  static std::mutex mu;
+  static void* ptrs[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RSVD_ECUDA;
+  if (dev < 0 || dev >= 64) return RSVD_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_build_scratch) != cudaSuccess || p == nullptr) return RSVD_ECUDA;
+    ptrs[dev] = p;
+  }
+  *out = ptrs[dev];
+  return RSVD_OK;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+extern "C" int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, const void* templates, int N_B, int H,
+                                             double* U, double* eig, void* stream) {
+  using namespace rsvd;
+  int rc = check_grid(R, Q, H);
+  if (rc != RSVD_OK) return rc;
+  if (!w || !templates || !U || !eig || N_B <= 0) return RSVD_EINVAL;
+  if (((uintptr_t)templates & 7u) || ((uintptr_t)U & 7u) || ((uintptr_t)eig & 7u)) return RSVD_EINVAL;
+  const BuildPlan pl = make_plan_capped(R, N_B, kStaticScratchBytes);
+  if (pl.total > kStaticScratchBytes) return RSVD_EUNSUPPORTED;  // R too large for the fixed scratch
+  ReduceParams rp{};
+  for (int r = 0; r < R; ++r) {
+    if (!(w[r] >= 0.0)) return RSVD_EINVAL;
+    rp.sw[r] = sqrt(w[r]);
+  }
+  void* scratch = nullptr;
+  if ((rc = static_scratch(&scratch)) != RSVD_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(scratch);
+  double* partial = reinterpret_cast<double*>(ws + pl.off_partial);
+  double* C = reinterpret_cast<double*>(ws + pl.off_C);
+  double* A = reinterpret_cast<double*>(ws + pl.off_A);
+  double* V = reinterpret_cast<double*>(ws + pl.off_V);
+
+  dim3 grid(pl.nslices, pl.ntiles);
+  kernel_partial<<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.tiles1d, pl.nslices,
+                                            partial);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  rp.partial = partial;
+  rp.C = C;
+  rp.R = R;
+  rp.nslices = pl.nslices;
+  rp.N_B = N_B;
   kernel_reduce<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
   if ((rc = launch_status()) != RSVD_OK) return rc;
   const size_t need = (size_t)2 * R * R * sizeof(double);
