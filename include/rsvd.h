@@ -169,6 +169,42 @@ int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, int N_B, int
                     int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
                     void* stream);
 
+/* ------------------------------------------------------------------------
+ * Log-sum-exp alignment loss and its gradient (section 2.6 likelihood with
+ * the rotations, translations and templates marginalised):
+ *   L[n] = log sum_{j, t, m} exp(inv_sigma2 * X[n][t][j][m])
+ *
+ * rsvd_lse_rows: L[n] = log sum_j exp(lse[n][j]) from the per-pair lse of
+ *   rsvd_align_best.  lse dev float [N_A][N_B]; L dev float [N_A].
+ *
+ * rsvd_lse_backward: gradient of sum_n gL[n] L[n] with respect to the
+ * compressed rings, recomputing X (never stored). With
+ * P(m) = inv_sigma2 gL[n] exp(inv_sigma2 X(m) - L[n]) and
+ * G(q) = sum_m P(m) e^{+2 pi i q m / Q}:
+ *   gA[row][h][q] = 2 pi sum_j b_j(h, q) conj(G(q)),   gB[j][h][q] = 2 pi sum_{n,t} a_{n,t}(h, q) G(q)
+ * (convention d/dRe + i d/dIm of the full-spectrum coefficients), written in
+ * the packed slot layout of rsvd_compress (slot 0: the real q = 0 and q = Q/2
+ * terms). Supports Q in {128, 256, 512} and H <= 32 (else RSVD_EUNSUPPORTED).
+ *   L, gL      dev float [N_A]
+ *   gA         dev, layout of cA;  gB  dev, layout of cB
+ *   workspace  dev, >= rsvd_lse_backward_workspace_bytes(...) bytes, 16-byte aligned
+ *              (partial template gradients, summed in a fixed order: deterministic)
+ *
+ * rsvd_compress_backward: adjoint of rsvd_compress with U fixed: from the
+ * gradient gC with respect to the compressed rings (layout of `out` of
+ * rsvd_compress) to the gradient with respect to the polar samples,
+ *   gpolar dev complex64 [N][R][Q], Hermitian-paired (sample (r, q + Q/2) is the
+ *   conjugate of sample (r, q)).
+ * ------------------------------------------------------------------------ */
+int rsvd_lse_rows(const float* lse, int N_A, int N_B, float* L, void* stream);
+size_t rsvd_lse_backward_workspace_bytes(int N_A, int T, int N_B, int H, int Q);
+int rsvd_lse_backward(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
+                      int precision, float inv_sigma2, const float* L, const float* gL, void* gA,
+                      void* gB, void* workspace, size_t workspace_bytes, void* stream);
+int rsvd_compress_backward(int R, int Q, const double* k, const double* w, const double* U, int H,
+                           const void* gC, int N, const double* deltas, int T, int precision,
+                           void* gpolar, void* stream);
+
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).
  * Provided so callers can cross-check the fused kernel. */

@@ -17,8 +17,10 @@ tie each function to something other than itself live in
 from .rsvd_ref import (  # noqa: F401
     align_best,
     compress,
+    compress_adjoint,
     fb_coefficients,
     lse_loss,
+    lse_grad_compressed,
     lse_loss_grad,
     lse_pair_partials,
     principal_vectors,

@@ -180,26 +180,41 @@ def lse_loss_grad(images: np.ndarray, templates: np.ndarray, k: np.ndarray, w: n
         => G_F(r, psi) = (1/Q) sum_q exp(+2 pi i q psi / Q) G_a(r, q);
     F_t = F * phi_t  => G_F = sum_t conj(phi_t) G_F_t.
     """
-    nA, R, Q = images.shape
     A_t = translate(images, k, deltas)  # [nA, T, R, Q]
     a_c = compress(A_t, U, w)  # [nA, T, H, Q]
     b_c = compress(templates, U, w)  # [nB, H, Q]
+    loss, _, G_ac, G_bc = lse_grad_compressed(a_c, b_c, inv_sigma2)
+    G_images = compress_adjoint(G_ac, U, w, k, deltas)
+    G_templates = compress_adjoint(G_bc[:, None], U, w, k, np.zeros((1, 2)))
+    return loss, G_images, G_templates
+
+
+def lse_grad_compressed(a_c: np.ndarray, b_c: np.ndarray, inv_sigma2: float, gL: np.ndarray | None = None):
+    """Loss sum_n gL_n L_n (gL = 1 by default) and its gradient with respect to the
+    compressed rings a_c [nA, T, H, Q] and b_c [nB, H, Q] (full spectrum, convention
+    dL/dRe + i dL/dIm). Returns (loss, L [nA], G_ac, G_bc)."""
+    Q = a_c.shape[-1]
     X = scores_compressed(a_c, b_c).real  # [nA, T, nB, Q]
-    loss, Ln = lse_loss(X, inv_sigma2)
-    P = np.exp(X * inv_sigma2 - Ln[:, None, None, None]) * inv_sigma2  # dL/dX
+    _, Ln = lse_loss(X, inv_sigma2)
+    g = np.ones_like(Ln) if gL is None else np.asarray(gL, dtype=np.float64)
+    P = np.exp(X * inv_sigma2 - Ln[:, None, None, None]) * (inv_sigma2 * g)[:, None, None, None]  # dL/dX
     G_Xhat = np.fft.ifft(P, axis=-1) * Q  # sum_m exp(+2 pi i q m / Q) P(m)
     G_bc = 2.0 * math.pi * np.einsum("nthq,ntjq->jhq", a_c, G_Xhat)
     G_ac = 2.0 * math.pi * np.einsum("jhq,ntjq->nthq", b_c, np.conj(G_Xhat))
+    return float(np.sum(g * Ln)), Ln, G_ac, G_bc
+
+
+def compress_adjoint(G_c: np.ndarray, U: np.ndarray, w: np.ndarray, k: np.ndarray, deltas: np.ndarray) -> np.ndarray:
+    """Adjoint of translate-then-compress, U fixed. G_c [n, T, H, Q] (gradient with
+    respect to the compressed rings, full spectrum) -> gradient with respect to the
+    polar samples [n, R, Q], in the convention G = dL/dRe + i dL/dIm:
+    G_a(r, q) = sqrt(w_r) sum_h U_rh G_c(h, q);  G_F_t(r, psi) = (1/Q) sum_q exp(+2 pi i q psi / Q) G_a(r, q);
+    G_F(r, psi) = sum_t conj(phi_t(r, psi)) G_F_t(r, psi)."""
+    Q = G_c.shape[-1]
     Wt = U * np.sqrt(w)[:, None]
-
-    def back_compress(G_c):
-        G_a = np.einsum("rh,...hq->...rq", Wt, G_c)
-        return np.fft.ifft(G_a, axis=-1)  # (1/Q) sum_q exp(+...) G_a
-
-    G_At = back_compress(G_ac)  # [nA, T, R, Q]
+    G_a = np.einsum("rh,nthq->ntrq", Wt, G_c)
+    G_Ft = np.fft.ifft(G_a, axis=-1)  # (1/Q) sum_q exp(+...) G_a
     psi = 2.0 * math.pi * np.arange(Q) / Q
     proj = deltas[:, 0][:, None] * np.cos(psi)[None, :] + deltas[:, 1][:, None] * np.sin(psi)[None, :]
     phase = np.exp(-1j * k[None, :, None] * proj[:, None, :])  # [T, R, Q]
-    G_images = np.einsum("ntrq,trq->nrq", G_At, np.conj(phase))
-    G_templates = back_compress(G_bc)
-    return loss, G_images, G_templates
+    return np.einsum("ntrq,trq->nrq", G_Ft, np.conj(phase))

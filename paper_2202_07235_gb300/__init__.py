@@ -8,12 +8,17 @@ this package is the thin Python binding: ``build_radial_svd``, ``compress``,
 from ._native import RSVDError, lib, lib_path  # noqa: F401
 from .api import (  # noqa: F401
     FP32,
+    LSEAlign,
     align_best,
     align_scores,
     build_radial_svd,
     build_radial_svd_noalloc,
     build_workspace_bytes,
     compress,
+    compress_backward,
     compressed_bytes,
+    lse_align,
+    lse_backward,
+    lse_rows,
     status,
 )

@@ -132,6 +132,81 @@ def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H
     return best, arg, lse
 
 
+def lse_rows(lse: torch.Tensor, stream=None) -> torch.Tensor:
+    """L[n] = log sum_j exp(lse[n][j])."""
+    N_A, N_B = lse.shape
+    L = torch.empty((N_A,), dtype=torch.float32, device=lse.device)
+    check(lib().rsvd_lse_rows(_ptr(lse), N_A, N_B, _ptr(L), _stream(stream)), "rsvd_lse_rows")
+    return L
+
+
+def lse_backward(cA, N_A, T, cB, N_B, H, Q, inv_sigma2, L, gL, precision: int = FP32, stream=None):
+    """Gradients (gA, gB) of sum_n gL[n] L[n] with respect to the compressed rings."""
+    gA = torch.empty_like(cA)
+    gB = torch.empty_like(cB)
+    need = int(lib().rsvd_lse_backward_workspace_bytes(N_A, T, N_B, H, Q))
+    ws = torch.empty(max(need, 16), dtype=torch.uint8, device=cA.device)
+    check(lib().rsvd_lse_backward(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, float(inv_sigma2), _ptr(L),
+                                  _ptr(gL), _ptr(gA), _ptr(gB), _ptr(ws), ws.numel(), _stream(stream)),
+          "rsvd_lse_backward")
+    return gA, gB
+
+
+def compress_backward(k, w, U: torch.Tensor, gC: torch.Tensor, N: int, R: int, Q: int, deltas=None,
+                      precision: int = FP32, stream=None) -> torch.Tensor:
+    """Gradient with respect to the polar samples (complex64 [N, R, Q]) from the
+    gradient with respect to the compressed rings (layout of compress)."""
+    H = U.shape[1]
+    ka, kp = _host_f64(k)
+    wa, wp = _host_f64(w)
+    if deltas is None:
+        T, dp = 1, None
+    else:
+        da, dp = _host_f64(deltas)
+        T = da.reshape(-1, 2).shape[0]
+    out = torch.empty((N, R, Q), dtype=torch.complex64, device=gC.device)
+    check(lib().rsvd_compress_backward(R, Q, kp, wp, _ptr(U), H, _ptr(gC), N, dp, T, precision, _ptr(out),
+                                       _stream(stream)), "rsvd_compress_backward")
+    return out
+
+
+class LSEAlign(torch.autograd.Function):
+    """Per-image log-sum-exp alignment loss L[n] = log sum_{j,t,m} exp(X/sigma^2)
+    as a differentiable function of the polar samples of the images and the
+    templates (principal vectors U held fixed). Forward: compress, fused
+    alignment with log-sum-exp, row reduction. Backward: rsvd_lse_backward
+    (recomputes X) then rsvd_compress_backward for both sets."""
+
+    @staticmethod
+    def forward(ctx, images, templates, U, k, w, deltas, inv_sigma2):
+        N_A, R, Q = images.shape
+        N_B = templates.shape[0]
+        H = U.shape[1]
+        cA = compress(k, w, U, images, deltas=deltas)
+        cB = compress(k, w, U, templates)
+        T = cA.shape[0] // N_A
+        _, _, lse = align_best(cA, N_A, T, cB, N_B, H, Q, inv_sigma2=inv_sigma2, want_lse=True)
+        L = lse_rows(lse)
+        ctx.save_for_backward(U, cA, cB, L)
+        ctx.cfg = (k, w, deltas, inv_sigma2, N_A, N_B, T, H, R, Q)
+        return L
+
+    @staticmethod
+    def backward(ctx, gL):
+        U, cA, cB, L = ctx.saved_tensors
+        k, w, deltas, inv_sigma2, N_A, N_B, T, H, R, Q = ctx.cfg
+        gL = gL.contiguous().to(torch.float32)
+        gA, gB = lse_backward(cA, N_A, T, cB, N_B, H, Q, inv_sigma2, L, gL)
+        G_img = compress_backward(k, w, U, gA, N_A, R, Q, deltas=deltas)
+        G_tmp = compress_backward(k, w, U, gB, N_B, R, Q)
+        return G_img, G_tmp, None, None, None, None, None
+
+
+def lse_align(images, templates, U, k, w, deltas=None, inv_sigma2: float = 1.0) -> torch.Tensor:
+    """Differentiable per-image log-sum-exp alignment loss (see LSEAlign)."""
+    return LSEAlign.apply(images, templates, U, k, w, deltas, inv_sigma2)
+
+
 def status(stream=None) -> None:
     """Synchronises the stream and raises if a kernel recorded a device-side failure."""
     check(lib().rsvd_status(_stream(stream)), "rsvd_status")

@@ -79,10 +79,11 @@ __device__ __forceinline__ constexpr float2 twiddle(int k) {
   return make_float2(unit_cos32(((k % N + N) % N) * (32 / N)), -unit_sin32(((k % N + N) % N) * (32 / N)));
 }
 
-// In-register forward DFT of length N (power of two, N <= 32):
-// x[k] <- sum_n x[n] exp(-2 pi i n k / N). Radix-2 decimation in time on a
-// bit-reversed copy; every index and twiddle is a compile-time constant.
-template <int N>
+// In-register DFT of length N (power of two, N <= 32):
+// x[k] <- sum_n x[n] exp(-+2 pi i n k / N) (minus sign unless kInv). Radix-2
+// decimation in time on a bit-reversed copy; every index and twiddle is a
+// compile-time constant.
+template <int N, bool kInv = false>
 struct RegDft {
   static constexpr int kLog2 = (N <= 1) ? 0 : 1 + RegDft<N / 2>::kLog2;
   static __device__ __forceinline__ int brev(int i) {
@@ -101,14 +102,15 @@ struct RegDft {
       for (int base = 0; base < N; base += 2 * half) {
 #pragma unroll
         for (int j = 0; j < half; ++j) {
-          const float2 w = twiddle<N>(j * (N / (2 * half)));
+          float2 w = twiddle<N>(j * (N / (2 * half)));
+          if (kInv) w.y = -w.y;
           float2 a = y[base + j];
           float2 b = y[base + j + half];
           float2 bw;
           if (j == 0) {
             bw = b;
-          } else if (2 * j == half) {  // W = -i
-            bw = cmul_mi(b);
+          } else if (2 * j == half) {  // W = -i (forward) or +i (inverse)
+            bw = kInv ? make_float2(-b.y, b.x) : cmul_mi(b);
           } else {
             bw = cmul(b, w);
           }
@@ -121,8 +123,8 @@ struct RegDft {
     for (int i = 0; i < N; ++i) x[i] = y[i];
   }
 };
-template <>
-struct RegDft<1> {
+template <bool kInv>
+struct RegDft<1, kInv> {
   static constexpr int kLog2 = 0;
   static __device__ __forceinline__ void run(float2 (&)[1]) {}
 };
