@@ -62,6 +62,9 @@ struct FftSplit<256> {
 
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
+inline int igcd(int a, int b) { return b == 0 ? a : igcd(b, a % b); }
+// Images per CTA such that its IMG*T rows fill whole passes of RP rows.
+inline int images_per_cta(int RP, int T) { return RP / igcd(RP, T); }
 
 // Pair-region stride (float2): at least the spectrum (S) and the padded
 // exchange buffer (P1 rows of P2+1); when a warp holds several pairs (each
@@ -360,7 +363,7 @@ int launch_fused_cfg(const FusedParams& p0, cudaStream_t stream) {
     return RSVD_EUNSUPPORTED;
   } else {
     FusedParams p = p0;
-    p.IMG = cmax(1, C::RP / p.T);
+    p.IMG = images_per_cta(C::RP, p.T);
     const long long grid = ((long long)p.N_A + p.IMG - 1) / p.IMG;
     if (grid > 0x7fffffffLL) return RSVD_EUNSUPPORTED;
     if (cudaFuncSetAttribute(fused_align_kernel<S, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize,

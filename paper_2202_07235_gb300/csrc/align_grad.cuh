@@ -340,7 +340,7 @@ int launch_grad_cfg(bool tmpl, const GradParams& p0, int IMGT, cudaStream_t stre
   } else {
     GradParams p = p0;
     if (!tmpl) {
-      p.res_per_cta = cmax(1, C::RP / p.T) * p.T;  // whole images
+      p.res_per_cta = images_per_cta(C::RP, p.T) * p.T;  // whole images, whole passes
       const long long grid = ((long long)p.n_res + p.res_per_cta - 1) / p.res_per_cta;
       if (cudaFuncSetAttribute(grad_kernel<S, HP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)C::SMEM) != cudaSuccess)
