@@ -2,7 +2,10 @@
 // and the generic per-pair kernel.
 #include <math.h>
 
-#include "align_fused.cuh"
+#include <stdlib.h>
+#include <string.h>
+
+#include "align_ws.cuh"
 
 namespace rsvd {
 namespace {
@@ -38,11 +41,18 @@ extern "C" int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, i
   p.H = H;
   p.inv_sigma2 = inv_sigma2;
   const int HP = padded_h(H);
+  // RSVD_ALIGN_KERNEL=fused selects the single-role fused kernel where the
+  // warp-specialised one would be used (for cross-checks and measurements)
+  const char* pick = getenv("RSVD_ALIGN_KERNEL");
+  const bool classic = pick && strcmp(pick, "fused") == 0;
   rc = RSVD_EUNSUPPORTED;
   if (HP > 0) {
-    if (Q == 128) rc = launch_fused_s64(HP, p, st);
-    else if (Q == 256) rc = launch_fused_s128(HP, p, st);
-    else if (Q == 512) rc = launch_fused_s256(HP, p, st);
+    if (Q == 256 && !classic) rc = launch_ws_s128(HP, p, st);
+    if (rc == RSVD_EUNSUPPORTED) {
+      if (Q == 128) rc = launch_fused_s64(HP, p, st);
+      else if (Q == 256) rc = launch_fused_s128(HP, p, st);
+      else if (Q == 512) rc = launch_fused_s256(HP, p, st);
+    }
   }
   if (rc == RSVD_EUNSUPPORTED) rc = align_best_pairwise(cA, N_A, T, cB, N_B, H, Q, inv_sigma2, best, arg, lse, st);
   return rc;

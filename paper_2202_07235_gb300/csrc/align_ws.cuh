@@ -1,0 +1,344 @@
+// Warp-specialised fused scoring kernel (rsvd_align_best, FP32, Q/2 <= 128).
+//
+// Same arithmetic as fused_align_kernel (eq. image_innerproduct_pm Steps 1-2,
+// section 2.7 argmax, section 2.6 log-sum-exp), with the two phases running
+// concurrently in different warps instead of alternating behind CTA-wide
+// barriers:
+// * contraction warps (CT threads = GC row groups x S angular slots) hold RT
+//   image rows per slot in registers and write the half spectra of RP x TB
+//   (row, template) pairs into one of two spectrum buffers;
+// * FFT warps (256 threads, P2 lanes per pair) take a full buffer, run the C2R
+//   FFT and the max/argmax/log-sum-exp of each pair, release the buffer, and
+//   merge the rows of each image into the outputs.
+// Hand-offs use named barriers (FULL[i]: contraction -> FFT, FREE[i]: FFT ->
+// contraction). Templates arrive by bulk asynchronous copies (TMA) issued by
+// one contraction thread into a double buffer, completing on mbarriers whose
+// waits are bounded by a clock budget (a timeout is recorded in the status
+// word and the CTA finishes without further copies).
+#pragma once
+
+#include "align_fused.cuh"
+#include "ptx_sync.cuh"
+
+namespace rsvd {
+
+template <int S, int HP>
+struct WsCfg {
+  static constexpr int P1 = FftSplit<S>::P1, P2 = FftSplit<S>::P2, F = P2, RR = P1 / P2;
+  static constexpr int RT = cmax(1, cmin(4, 36 / HP));  // image rows per contraction thread
+  static constexpr int GC = cmax(1, 256 / S);            // contraction row groups
+  static constexpr int CT = GC * S;                      // contraction threads
+  static constexpr int FT = 256;                         // FFT threads
+  static constexpr int NT = CT + FT;
+  static constexpr int RP = GC * RT;                     // rows per pass
+  static constexpr int PGF = FT / F;                     // pairs per FFT round
+  static constexpr int XP = P2 + 1;
+  static constexpr int SP = pair_stride(S, P1, P2);
+  static constexpr int PER_TB = 2 * HP * S * 8 + 2 * RP * SP * 8 + 24 * RP;
+  static constexpr int TB_SMEM = (200 * 1024 - 2 * S * 8 - 64) / PER_TB;
+  static constexpr int TB = cmax(1, cmin(TB_SMEM, cmax(1, PGF / RP)));  // templates per batch
+  static constexpr int PAIRS = RP * TB;
+  static constexpr size_t SMEM = (size_t)2 * TB * HP * S * 8 + (size_t)2 * PAIRS * SP * 8 + (size_t)2 * S * 8 +
+                                 (size_t)2 * 3 * PAIRS * 4 + 64;
+  static constexpr bool kFits = SMEM <= 227 * 1024 && S <= 128 && TB_SMEM >= 1;
+};
+
+// clock budget of one bounded wait (about half a second at 2 GHz)
+constexpr long long kWaitBudget = 1ll << 30;
+
+enum : int { kBarCW = 1, kBarFW = 2, kBarFull0 = 3, kBarFree0 = 5 };
+
+template <int S, int HP>
+__global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __grid_constant__ FusedParams p) {
+  using C = WsCfg<S, HP>;
+  constexpr int M = S, Q = 2 * S, P1 = C::P1, P2 = C::P2, RP = C::RP, RT = C::RT, TB = C::TB;
+  constexpr int CT = C::CT, FT = C::FT, NT = C::NT, SP = C::SP, XP = C::XP, F = C::F, RR = C::RR;
+  constexpr int PAIRS = C::PAIRS, PGF = C::PGF;
+  static_assert(P1 * P2 == M && P1 % P2 == 0 && 32 % F == 0, "bad FFT split");
+
+  extern __shared__ __align__(128) unsigned char ws_smem[];
+  float2* tbuf = reinterpret_cast<float2*>(ws_smem);   // [2][TB][HP][S], rows h >= H zero
+  float2* spec = tbuf + 2 * TB * HP * S;               // [2][PAIRS][SP]
+  float2* twQ = spec + 2 * PAIRS * SP;                 // [M]
+  float2* tw1 = twQ + M;                               // [M]
+  float* res = reinterpret_cast<float*>(tw1 + M);      // [2][3][PAIRS]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(res + 2 * 3 * PAIRS);  // [2]
+  int* abort_flag = reinterpret_cast<int*>(mbar + 2);
+
+  const int tid = threadIdx.x;
+  const int H = p.H, T = p.T, N_B = p.N_B;
+  const int img0 = blockIdx.x * p.IMG;
+  if (img0 >= p.N_A) return;
+  const int nimg = min(p.IMG, p.N_A - img0);
+  const int rows_cta = nimg * T;
+  const size_t row0 = (size_t)img0 * T;
+  const bool want_lse = (p.lse != nullptr);
+  const float two_pi = 6.28318530717958647692f;
+
+  for (int i = tid; i < M; i += NT) {
+    float sn, cs;
+    sincospif(-2.0f * (float)i / (float)Q, &sn, &cs);
+    twQ[i] = make_float2(cs, sn);
+    const int k1 = i / P2, t = i % P2;
+    sincospif(-2.0f * (float)(t * k1) / (float)M, &sn, &cs);
+    tw1[i] = make_float2(cs, sn);
+  }
+  for (int i = tid; i < 2 * TB * (HP - H) * S; i += NT) {
+    const int slot = i / ((HP - H) * S), rem = i % ((HP - H) * S);
+    tbuf[(size_t)slot * HP * S + (size_t)H * S + rem] = make_float2(0.f, 0.f);
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int nbatch = (N_B + TB - 1) / TB;
+  const int passes = (rows_cta + RP - 1) / RP;
+  const int total = passes * nbatch;
+
+  if (tid < CT) {
+    // ======================= contraction warps =======================
+    const int g = tid / S, s = tid % S;
+    const bool slot0 = (s == 0);
+    auto issue = [&](int it) {
+      const int b = it % nbatch;
+      const int j0 = b * TB;
+      const int nb = min(TB, N_B - j0);
+      const int buf = it & 1;
+      const uint32_t per = (uint32_t)H * S * 8;
+      mbar_arrive_expect_tx(&mbar[buf], per * nb);
+      if (HP == H) {
+        bulk_g2s(tbuf + (size_t)buf * TB * HP * S, p.cB + (size_t)j0 * H * S, per * nb, &mbar[buf]);
+      } else {
+        for (int jj = 0; jj < nb; ++jj)
+          bulk_g2s(tbuf + (size_t)(buf * TB + jj) * HP * S, p.cB + (size_t)(j0 + jj) * H * S, per, &mbar[buf]);
+      }
+    };
+    if (tid == 0 && total > 0) issue(0);
+    int waited_upto = -1;  // iterations whose copies this thread has seen complete
+    float2 a[RT][HP];
+    for (int it = 0; it < total; ++it) {
+      const int ps = (it / nbatch) * RP;
+      const int b = it % nbatch;
+      const int nb = min(TB, N_B - b * TB);
+      named_sync(kBarCW, CT);  // every contraction thread is done with iteration it-1
+      const bool aborted = *reinterpret_cast<volatile int*>(abort_flag) != 0;
+      if (tid == 0 && it + 1 < total && !aborted) issue(it + 1);
+      if (b == 0) {
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          const int lr = ps + g * RT + i;
+          const bool valid = lr < rows_cta;
+          const float2* src = p.cA + ((row0 + (valid ? lr : 0)) * H) * S + s;
+#pragma unroll
+          for (int h = 0; h < HP; ++h) {
+            const float2 v = (valid && h < H) ? src[(size_t)h * S] : make_float2(0.f, 0.f);
+            a[i][h] = make_float2(two_pi * v.x, two_pi * v.y);
+          }
+        }
+      }
+      if (!aborted) {
+        if (mbar_wait_bounded(&mbar[it & 1], (it >> 1) & 1, kWaitBudget)) {
+          waited_upto = it;
+        } else {
+          record(p.status, kDevTimeout);
+          atomicExch(abort_flag, 1);
+        }
+      }
+      if (it >= 2) named_sync(kBarFree0 + (it & 1), CT + FT);
+      const float2* tb = tbuf + (size_t)(it & 1) * TB * HP * S + s;
+      float2* sp = spec + (size_t)(it & 1) * PAIRS * SP;
+#pragma unroll 1
+      for (int jj = 0; jj < TB; ++jj) {
+        if (jj < nb) {
+          float P[RT], Qa[RT], Ra[RT], Sa[RT];
+#pragma unroll
+          for (int i = 0; i < RT; ++i) P[i] = Qa[i] = Ra[i] = Sa[i] = 0.f;
+          const float2* bp = tb + (size_t)jj * HP * S;
+#pragma unroll
+          for (int h = 0; h < HP; ++h) {
+            const float2 bv = bp[h * S];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) {
+              P[i] = fmaf(a[i][h].x, bv.x, P[i]);
+              Qa[i] = fmaf(a[i][h].y, bv.y, Qa[i]);
+              Ra[i] = fmaf(a[i][h].x, bv.y, Ra[i]);
+              Sa[i] = fmaf(a[i][h].y, bv.x, Sa[i]);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < RT; ++i) {
+            const float re = slot0 ? P[i] : P[i] + Qa[i];
+            const float im = slot0 ? Qa[i] : Ra[i] - Sa[i];
+            sp[((g * RT + i) * TB + jj) * SP + s] = make_float2(re, im);
+          }
+        }
+      }
+      named_arrive(kBarFull0 + (it & 1), CT + FT);
+    }
+    // copies issued but not waited for (only after a timeout): wait, bounded
+    if (tid == 0 && total > 0 && waited_upto < total - 1) {
+      const int last = total - 1;
+      (void)mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, kWaitBudget);
+    }
+  } else {
+    // =========================== FFT warps ===========================
+    const int ftid = tid - CT;
+    const int ft = ftid % F;
+    const float s2 = p.inv_sigma2;
+    const float log2e = 1.44269504088896340736f;
+    for (int it = 0; it < total; ++it) {
+      const int ps = (it / nbatch) * RP;
+      const int b = it % nbatch;
+      const int j0 = b * TB;
+      const int nb = min(TB, N_B - j0);
+      named_sync(kBarFull0 + (it & 1), CT + FT);
+      float* rs = res + (it & 1) * 3 * PAIRS;
+      const float2* specb = spec + (size_t)(it & 1) * PAIRS * SP;
+#pragma unroll 1
+      for (int pb = 0; pb < PAIRS; pb += PGF) {
+        const int pr = pb + ftid / F;
+        const int rl = pr / TB, jj = pr % TB;
+        const bool ok = (pr < PAIRS) && (jj < nb) && (ps + rl < rows_cta);
+        float2* sp = const_cast<float2*>(specb) + (size_t)(pr < PAIRS ? pr : 0) * SP;
+        float2 z[P1];
+        if (ok) {
+#pragma unroll
+          for (int q1 = 0; q1 < P1; ++q1) {
+            const int k = ft + P2 * q1;
+            float2 A, B;
+            if (q1 == 0 && ft == 0) {
+              const float2 v = sp[0];
+              A = make_float2(v.x, 0.f);
+              B = make_float2(v.y, 0.f);
+            } else {
+              A = sp[k];
+              B = cconj(sp[M - k]);
+            }
+            const float2 d = cmul(csub(A, B), twQ[k]);
+            z[q1] = make_float2(A.x + B.x - d.y, A.y + B.y + d.x);
+          }
+          RegDft<P1>::run(z);
+#pragma unroll
+          for (int k1 = 1; k1 < P1; ++k1) z[k1] = cmul(z[k1], tw1[k1 * P2 + ft]);
+        }
+        __syncwarp();
+        if (ok) {
+#pragma unroll
+          for (int k1 = 0; k1 < P1; ++k1) sp[k1 * XP + ft] = z[k1];
+        }
+        __syncwarp();
+        float2 y[RR][P2];
+        float bv = -INFINITY;
+        int bj = 0;
+        if (ok) {
+#pragma unroll
+          for (int i = 0; i < RR; ++i) {
+#pragma unroll
+            for (int tp = 0; tp < P2; ++tp) y[i][tp] = sp[(ft * RR + i) * XP + tp];
+            RegDft<P2>::run(y[i]);
+          }
+#pragma unroll
+          for (int k2 = 0; k2 < P2; ++k2) {
+#pragma unroll
+            for (int i = 0; i < RR; ++i) {
+              const int j = (k2 * RR + i) * 2;
+              if (y[i][k2].x > bv) {
+                bv = y[i][k2].x;
+                bj = j;
+              }
+              if (y[i][k2].y > bv) {
+                bv = y[i][k2].y;
+                bj = j + 1;
+              }
+            }
+          }
+        }
+        int bm = ok ? 2 * (ft * RR + (bj >> 1) % RR + P1 * ((bj >> 1) / RR)) + (bj & 1) : 0x7fffffff;
+        argmax_warp_reduce(bv, bm, F);
+        float lsev = 0.f;
+        if (want_lse) {
+          float sum = 0.f;
+          if (ok) {
+            const float c = s2 * log2e, off = -c * bv;
+#pragma unroll
+            for (int i = 0; i < RR; ++i)
+#pragma unroll
+              for (int k2 = 0; k2 < P2; ++k2)
+                sum += exp2f(fmaf(c, y[i][k2].x, off)) + exp2f(fmaf(c, y[i][k2].y, off));
+          }
+#pragma unroll
+          for (int off = F / 2; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off, F);
+          lsev = s2 * bv + logf(sum);
+        }
+        if (ok && ft == 0) {
+          rs[pr] = bv;
+          reinterpret_cast<int*>(rs + PAIRS)[pr] = bm;
+          rs[2 * PAIRS + pr] = lsev;
+        }
+      }
+      if (it + 2 < total) named_arrive(kBarFree0 + (it & 1), CT + FT);
+      named_sync(kBarFW, FT);  // every pair of this batch is reduced
+      // ---- merge rows of each image, combine with earlier passes, store ----
+      const float* rv = rs;
+      const int* ri = reinterpret_cast<const int*>(rs + PAIRS);
+      const float* rlse = rs + 2 * PAIRS;
+      const int il0 = ps / T;
+      const int il1 = min(nimg - 1, (ps + RP - 1) / T);
+      const int nitems = (il1 - il0 + 1) * nb;
+      for (int item = ftid; item < nitems; item += FT) {
+        const int il = il0 + item / nb, jj = item % nb;
+        const int rlo = max(il * T - ps, 0), rhi = min((il + 1) * T - ps, RP);
+        float vb = -INFINITY, mm = -INFINITY, sm = 0.f;
+        int ib = 0x7fffffff;
+        for (int r_ = rlo; r_ < rhi; ++r_) {
+          const int pr = r_ * TB + jj;
+          const int t = ps + r_ - il * T;
+          const float v = rv[pr];
+          if (v > vb || r_ == rlo) {
+            vb = v;
+            ib = t * Q + ri[pr];
+          }
+          if (want_lse) lse_merge(mm, sm, rlse[pr], 1.0f);
+        }
+        const size_t o = (size_t)(img0 + il) * N_B + j0 + jj;
+        if (il * T < ps) {
+          const float ov = p.best[o];
+          if (!(vb > ov)) {
+            vb = ov;
+            ib = p.arg[o];
+          }
+          if (want_lse) lse_merge(mm, sm, p.lse[o], 1.0f);
+        }
+        p.best[o] = vb;
+        p.arg[o] = ib;
+        if (want_lse) p.lse[o] = mm + logf(sm);
+      }
+    }
+  }
+}
+
+template <int S, int HP>
+int launch_ws_cfg(const FusedParams& p0, cudaStream_t stream) {
+  using C = WsCfg<S, HP>;
+  if constexpr (!C::kFits) {
+    return RSVD_EUNSUPPORTED;
+  } else {
+    FusedParams p = p0;
+    p.IMG = images_per_cta(C::RP, p.T);
+    const long long grid = ((long long)p.N_A + p.IMG - 1) / p.IMG;
+    if (grid > 0x7fffffffLL) return RSVD_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(ws_align_kernel<S, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+        cudaSuccess)
+      return RSVD_ECUDA;
+    ws_align_kernel<S, HP><<<(unsigned)grid, C::NT, C::SMEM, stream>>>(p);
+    return launch_status();
+  }
+}
+
+RSVD_HIDDEN int launch_ws_s128(int HP, const FusedParams& p, cudaStream_t stream);
+
+}  // namespace rsvd
