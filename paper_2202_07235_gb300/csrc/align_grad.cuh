@@ -168,20 +168,29 @@ __global__ void __launch_bounds__(GradCfg<S, HP>::NT, 1) grad_kernel(const __gri
 #pragma unroll 1
       for (int jj = 0; jj < TB; ++jj) {
         if (jj < nb) {
-          float P[RT], Qa[RT], Ra[RT], Sa[RT];
+          // (P, Qa) = sum_h (a.x b.x, a.y b.y), (Ra, Sa) = sum_h (a.x b.y, a.y b.x): two packed
+          // FP32x2 FMAs per row and h; the swapped template value is shared by the RT rows
+          float2 PQ[RT], RS[RT];
 #pragma unroll
-          for (int i = 0; i < RT; ++i) P[i] = Qa[i] = Ra[i] = Sa[i] = 0.f;
+          for (int i = 0; i < RT; ++i) PQ[i] = RS[i] = make_float2(0.f, 0.f);
           const float2* bp = tb + (size_t)jj * HP * S;
 #pragma unroll
           for (int h = 0; h < HP; ++h) {
             const float2 bv = bp[h * S];
+            const float2 bs = make_float2(bv.y, bv.x);
 #pragma unroll
             for (int i = 0; i < RT; ++i) {
-              P[i] = fmaf(a[i][h].x, bv.x, P[i]);
-              Qa[i] = fmaf(a[i][h].y, bv.y, Qa[i]);
-              Ra[i] = fmaf(a[i][h].x, bv.y, Ra[i]);
-              Sa[i] = fmaf(a[i][h].y, bv.x, Sa[i]);
+              PQ[i] = __ffma2_rn(a[i][h], bv, PQ[i]);
+              RS[i] = __ffma2_rn(a[i][h], bs, RS[i]);
             }
+          }
+          float P[RT], Qa[RT], Ra[RT], Sa[RT];
+#pragma unroll
+          for (int i = 0; i < RT; ++i) {
+            P[i] = PQ[i].x;
+            Qa[i] = PQ[i].y;
+            Ra[i] = RS[i].x;
+            Sa[i] = RS[i].y;
           }
 #pragma unroll
           for (int i = 0; i < RT; ++i) {
