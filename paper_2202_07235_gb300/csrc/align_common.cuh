@@ -69,6 +69,42 @@ __device__ __forceinline__ void lse_warp_reduce(float& m, float& s, int width) {
   }
 }
 
+// Max and first-index argmax of N values given in increasing index order, as a
+// pairwise tree (depth log2 N): at each node the right child wins only if
+// strictly larger, so equal values keep the smaller index.
+template <int N>
+__device__ __forceinline__ void tree_argmax(const float (&v)[N], float& best, int& idx) {
+  static_assert((N & (N - 1)) == 0, "N must be a power of two");
+  float bv[N];
+  int bi[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    bv[i] = v[i];
+    bi[i] = i;
+  }
+#pragma unroll
+  for (int w = 1; w < N; w *= 2) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2 * w) {
+      const bool right = bv[i + w] > bv[i];
+      bv[i] = right ? bv[i + w] : bv[i];
+      bi[i] = right ? bi[i + w] : bi[i];
+    }
+  }
+  best = bv[0];
+  idx = bi[0];
+}
+
+// Pairwise-tree sum of N values.
+template <int N>
+__device__ __forceinline__ float tree_sum(float (&v)[N]) {
+#pragma unroll
+  for (int w = 1; w < N; w *= 2)
+#pragma unroll
+    for (int i = 0; i < N; i += 2 * w) v[i] += v[i + w];
+  return v[0];
+}
+
 // Generic per-pair path (align_pair.cu).
 RSVD_HIDDEN int align_best_pairwise(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
                                     float inv_sigma2, float* best, int32_t* arg, float* lse, cudaStream_t stream);

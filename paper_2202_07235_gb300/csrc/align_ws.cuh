@@ -35,10 +35,11 @@ struct WsCfg {
   static constexpr int XP = P2 + 1;
   static constexpr int SP = pair_stride(S, P1, P2);
   static constexpr int PER_TB = 2 * HP * S * 8 + 2 * RP * SP * 8 + 24 * RP;
-  static constexpr int TB_SMEM = (200 * 1024 - 2 * S * 8 - 64) / PER_TB;
+  static constexpr int TB_SMEM = (200 * 1024 - 2 * S * 8 - 64 - 2 * PGF * SP * 8) / PER_TB;
   static constexpr int TB = cmax(1, cmin(TB_SMEM, cmax(1, PGF / RP)));  // templates per batch
   static constexpr int PAIRS = RP * TB;
-  static constexpr size_t SMEM = (size_t)2 * TB * HP * S * 8 + (size_t)2 * PAIRS * SP * 8 + (size_t)2 * S * 8 +
+  static constexpr int SPB = PAIRS + (PGF - PAIRS % PGF) % PGF;  // pair regions per buffer (incl. dummies)
+  static constexpr size_t SMEM = (size_t)2 * TB * HP * S * 8 + (size_t)2 * SPB * SP * 8 + (size_t)2 * S * 8 +
                                  (size_t)2 * 3 * PAIRS * 4 + 64;
   static constexpr bool kFits = SMEM <= 227 * 1024 && S <= 128 && TB_SMEM >= 1;
 };
@@ -58,8 +59,8 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
 
   extern __shared__ __align__(128) unsigned char ws_smem[];
   float2* tbuf = reinterpret_cast<float2*>(ws_smem);   // [2][TB][HP][S], rows h >= H zero
-  float2* spec = tbuf + 2 * TB * HP * S;               // [2][PAIRS][SP]
-  float2* twQ = spec + 2 * PAIRS * SP;                 // [M]
+  float2* spec = tbuf + 2 * TB * HP * S;               // [2][SPB][SP] (PAIRS pairs + dummy regions)
+  float2* twQ = spec + 2 * C::SPB * SP;                 // [M]
   float2* tw1 = twQ + M;                               // [M]
   float* res = reinterpret_cast<float*>(tw1 + M);      // [2][3][PAIRS]
   uint64_t* mbar = reinterpret_cast<uint64_t*>(res + 2 * 3 * PAIRS);  // [2]
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
       }
       if (it >= 2) named_sync(kBarFree0 + (it & 1), CT + FT);
       const float2* tb = tbuf + (size_t)(it & 1) * TB * HP * S + s;
-      float2* sp = spec + (size_t)(it & 1) * PAIRS * SP;
+      float2* sp = spec + (size_t)(it & 1) * C::SPB * SP;
 #pragma unroll 1
       for (int jj = 0; jj < TB; ++jj) {
         if (jj < nb) {
@@ -206,81 +207,70 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
       const int nb = min(TB, N_B - j0);
       named_sync(kBarFull0 + (it & 1), CT + FT);
       float* rs = res + (it & 1) * 3 * PAIRS;
-      const float2* specb = spec + (size_t)(it & 1) * PAIRS * SP;
+      const float2* specb = spec + (size_t)(it & 1) * C::SPB * SP;
 #pragma unroll 1
       for (int pb = 0; pb < PAIRS; pb += PGF) {
         const int pr = pb + ftid / F;
         const int rl = pr / TB, jj = pr % TB;
         const bool ok = (pr < PAIRS) && (jj < nb) && (ps + rl < rows_cta);
-        float2* sp = const_cast<float2*>(specb) + (size_t)(pr < PAIRS ? pr : 0) * SP;
+        // groups without a pair (pr >= PAIRS) run on their own dummy region
+        // (pr < SPB), keeping control flow uniform
+        float2* sp = const_cast<float2*>(specb) + (size_t)pr * SP;
         float2 z[P1];
-        if (ok) {
 #pragma unroll
-          for (int q1 = 0; q1 < P1; ++q1) {
-            const int k = ft + P2 * q1;
-            float2 A, B;
-            if (q1 == 0 && ft == 0) {
-              const float2 v = sp[0];
-              A = make_float2(v.x, 0.f);
-              B = make_float2(v.y, 0.f);
-            } else {
-              A = sp[k];
-              B = cconj(sp[M - k]);
-            }
-            const float2 d = cmul(csub(A, B), twQ[k]);
-            z[q1] = make_float2(A.x + B.x - d.y, A.y + B.y + d.x);
+        for (int q1 = 0; q1 < P1; ++q1) {
+          const int k = ft + P2 * q1;
+          float2 A = sp[k];
+          float2 B = cconj(sp[M - k]);
+          if (q1 == 0) {  // k = 0 on lane 0: slot 0 packs the real X_hat(0), X_hat(Q/2)
+            const bool k0 = (ft == 0);
+            const float2 v = A;
+            A = k0 ? make_float2(v.x, 0.f) : A;
+            B = k0 ? make_float2(v.y, 0.f) : B;
           }
-          RegDft<P1>::run(z);
-#pragma unroll
-          for (int k1 = 1; k1 < P1; ++k1) z[k1] = cmul(z[k1], tw1[k1 * P2 + ft]);
+          const float2 d = cmul(csub(A, B), twQ[k]);
+          z[q1] = make_float2(A.x + B.x - d.y, A.y + B.y + d.x);
         }
+        RegDft<P1>::run(z);
+#pragma unroll
+        for (int k1 = 1; k1 < P1; ++k1) z[k1] = cmul(z[k1], tw1[k1 * P2 + ft]);
         __syncwarp();
-        if (ok) {
 #pragma unroll
-          for (int k1 = 0; k1 < P1; ++k1) sp[k1 * XP + ft] = z[k1];
-        }
+        for (int k1 = 0; k1 < P1; ++k1) sp[k1 * XP + ft] = z[k1];
         __syncwarp();
         float2 y[RR][P2];
-        float bv = -INFINITY;
-        int bj = 0;
-        if (ok) {
+#pragma unroll
+        for (int i = 0; i < RR; ++i) {
+#pragma unroll
+          for (int tp = 0; tp < P2; ++tp) y[i][tp] = sp[(ft * RR + i) * XP + tp];
+          RegDft<P2>::run(y[i]);
+        }
+        // outputs in increasing m: m = 2 (ft*RR + i + P1*k2) + e at leaf (k2*RR + i)*2 + e
+        float vals[2 * P1];
+#pragma unroll
+        for (int k2 = 0; k2 < P2; ++k2)
 #pragma unroll
           for (int i = 0; i < RR; ++i) {
-#pragma unroll
-            for (int tp = 0; tp < P2; ++tp) y[i][tp] = sp[(ft * RR + i) * XP + tp];
-            RegDft<P2>::run(y[i]);
+            vals[(k2 * RR + i) * 2] = y[i][k2].x;
+            vals[(k2 * RR + i) * 2 + 1] = y[i][k2].y;
           }
-#pragma unroll
-          for (int k2 = 0; k2 < P2; ++k2) {
-#pragma unroll
-            for (int i = 0; i < RR; ++i) {
-              const int j = (k2 * RR + i) * 2;
-              if (y[i][k2].x > bv) {
-                bv = y[i][k2].x;
-                bj = j;
-              }
-              if (y[i][k2].y > bv) {
-                bv = y[i][k2].y;
-                bj = j + 1;
-              }
-            }
-          }
+        float bv;
+        int bj;
+        tree_argmax<2 * P1>(vals, bv, bj);
+        int bm = 2 * (ft * RR + (bj >> 1) % RR + P1 * ((bj >> 1) / RR)) + (bj & 1);
+        if (!ok) {
+          bv = -INFINITY;
+          bm = 0x7fffffff;
         }
-        int bm = ok ? 2 * (ft * RR + (bj >> 1) % RR + P1 * ((bj >> 1) / RR)) + (bj & 1) : 0x7fffffff;
         argmax_warp_reduce(bv, bm, F);
         float lsev = 0.f;
         if (want_lse) {
-          float sum = 0.f;
-          if (ok) {
-            const float c = s2 * log2e, off = -c * bv;
+          const float c = s2 * log2e, off = -c * bv;
 #pragma unroll
-            for (int i = 0; i < RR; ++i)
+          for (int t = 0; t < 2 * P1; ++t) vals[t] = exp2f(fmaf(c, vals[t], off));
+          float sum = ok ? tree_sum<2 * P1>(vals) : 0.f;
 #pragma unroll
-              for (int k2 = 0; k2 < P2; ++k2)
-                sum += exp2f(fmaf(c, y[i][k2].x, off)) + exp2f(fmaf(c, y[i][k2].y, off));
-          }
-#pragma unroll
-          for (int off = F / 2; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off, F);
+          for (int o = F / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, F);
           lsev = s2 * bv + logf(sum);
         }
         if (ok && ft == 0) {
