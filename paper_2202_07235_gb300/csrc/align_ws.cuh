@@ -35,7 +35,7 @@ struct WsCfg {
   static constexpr int XP = P2 + 1;
   static constexpr int SP = pair_stride(S, P1, P2);
   static constexpr int PER_TB = 2 * HP * S * 8 + 2 * RP * SP * 8 + 24 * RP;
-  static constexpr int TB_SMEM = (200 * 1024 - 2 * S * 8 - 64 - 2 * PGF * SP * 8) / PER_TB;
+  static constexpr int TB_SMEM = (200 * 1024 - 2 * S * 8 - 64) / PER_TB;
   static constexpr int TB = cmax(1, cmin(TB_SMEM, cmax(1, PGF / RP)));  // templates per batch
   static constexpr int PAIRS = RP * TB;
   static constexpr int SPB = PAIRS + (PGF - PAIRS % PGF) % PGF;  // pair regions per buffer (incl. dummies)
