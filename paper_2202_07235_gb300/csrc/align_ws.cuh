@@ -200,12 +200,93 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
     const int ft = ftid % F;
     const float s2 = p.inv_sigma2;
     const float log2e = 1.44269504088896340736f;
+    // merge items of a batch: (image, template) pairs, spread one per warp lane 0
+    // first (item i -> thread (i % warps) * 32 + i / warps)
+    constexpr int FWARPS = FT / 32;
+    const int my_item = (ftid % 32) * FWARPS + ftid / 32;
+    struct MergeSlot {
+      int it, item;
+      bool active, rmw, fetched;
+      float ov, ol;
+      int oi;
+    };
+    auto fetch = [&](MergeSlot& m, size_t o) {
+      m.ov = p.best[o];
+      m.oi = p.arg[o];
+      m.ol = want_lse ? p.lse[o] : 0.f;
+      m.fetched = true;
+    };
+    auto merge_prepare = [&](int it) {
+      MergeSlot m{};
+      m.it = it;
+      m.item = my_item;
+      const int ps = (it / nbatch) * RP;
+      const int j0 = (it % nbatch) * TB;
+      const int nb = min(TB, N_B - j0);
+      const int il0 = ps / T;
+      const int il1 = min(nimg - 1, (ps + RP - 1) / T);
+      const int nitems = (il1 - il0 + 1) * nb;
+      m.active = my_item < nitems;
+      m.rmw = false;
+      if (m.active) {
+        const int il = il0 + my_item / nb, jj = my_item % nb;
+        if (il * T < ps) {  // an earlier pass stored smaller t of this image
+          m.rmw = true;
+          // with several batches per pass that store was committed at least one
+          // FULL sync ago, so it can be fetched now; with one batch it is
+          // committed in this same iteration by another thread: fetch at commit
+          if (nbatch >= 2) fetch(m, (size_t)(img0 + il) * N_B + j0 + jj);
+        }
+      }
+      return m;
+    };
+    auto merge_commit = [&](MergeSlot& m, const float* rs) {
+      if (!m.active) return;
+      const int ps = (m.it / nbatch) * RP;
+      const int j0 = (m.it % nbatch) * TB;
+      const int nb = min(TB, N_B - j0);
+      const int il = ps / T + m.item / nb, jj = m.item % nb;
+      const float* rv = rs;
+      const int* ri = reinterpret_cast<const int*>(rs + PAIRS);
+      const float* rlse = rs + 2 * PAIRS;
+      const int rlo = max(il * T - ps, 0), rhi = min((il + 1) * T - ps, RP);
+      float vb = -INFINITY, mm = -INFINITY, sm = 0.f;
+      int ib = 0x7fffffff;
+      for (int r_ = rlo; r_ < rhi; ++r_) {
+        const int pr = r_ * TB + jj;
+        const int t = ps + r_ - il * T;
+        const float v = rv[pr];
+        if (v > vb || r_ == rlo) {  // increasing t: ties keep the earlier index
+          vb = v;
+          ib = t * Q + ri[pr];
+        }
+        if (want_lse) lse_merge(mm, sm, rlse[pr], 1.0f);
+      }
+      const size_t o = (size_t)(img0 + il) * N_B + j0 + jj;
+      if (m.rmw) {
+        if (!m.fetched) fetch(m, o);
+        if (!(vb > m.ov)) {
+          vb = m.ov;
+          ib = m.oi;
+        }
+        if (want_lse) lse_merge(mm, sm, m.ol, 1.0f);
+      }
+      p.best[o] = vb;
+      p.arg[o] = ib;
+      if (want_lse) p.lse[o] = mm + logf(sm);
+    };
+    // Merge of batch `it` happens in iteration it+1, right after the FULL sync
+    // (all FFT threads are then past batch it); its read-modify-write operands
+    // are prefetched into registers one iteration earlier.
+    MergeSlot ms;
     for (int it = 0; it < total; ++it) {
       const int ps = (it / nbatch) * RP;
       const int b = it % nbatch;
       const int j0 = b * TB;
       const int nb = min(TB, N_B - j0);
       named_sync(kBarFull0 + (it & 1), CT + FT);
+      if (it > 0) merge_commit(ms, res + ((it - 1) & 1) * 3 * PAIRS);
+      ms = merge_prepare(it);
       float* rs = res + (it & 1) * 3 * PAIRS;
       const float2* specb = spec + (size_t)(it & 1) * C::SPB * SP;
 #pragma unroll 1
@@ -280,42 +361,10 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
         }
       }
       if (it + 2 < total) named_arrive(kBarFree0 + (it & 1), CT + FT);
-      named_sync(kBarFW, FT);  // every pair of this batch is reduced
-      // ---- merge rows of each image, combine with earlier passes, store ----
-      const float* rv = rs;
-      const int* ri = reinterpret_cast<const int*>(rs + PAIRS);
-      const float* rlse = rs + 2 * PAIRS;
-      const int il0 = ps / T;
-      const int il1 = min(nimg - 1, (ps + RP - 1) / T);
-      const int nitems = (il1 - il0 + 1) * nb;
-      for (int item = ftid; item < nitems; item += FT) {
-        const int il = il0 + item / nb, jj = item % nb;
-        const int rlo = max(il * T - ps, 0), rhi = min((il + 1) * T - ps, RP);
-        float vb = -INFINITY, mm = -INFINITY, sm = 0.f;
-        int ib = 0x7fffffff;
-        for (int r_ = rlo; r_ < rhi; ++r_) {
-          const int pr = r_ * TB + jj;
-          const int t = ps + r_ - il * T;
-          const float v = rv[pr];
-          if (v > vb || r_ == rlo) {
-            vb = v;
-            ib = t * Q + ri[pr];
-          }
-          if (want_lse) lse_merge(mm, sm, rlse[pr], 1.0f);
-        }
-        const size_t o = (size_t)(img0 + il) * N_B + j0 + jj;
-        if (il * T < ps) {
-          const float ov = p.best[o];
-          if (!(vb > ov)) {
-            vb = ov;
-            ib = p.arg[o];
-          }
-          if (want_lse) lse_merge(mm, sm, p.lse[o], 1.0f);
-        }
-        p.best[o] = vb;
-        p.arg[o] = ib;
-        if (want_lse) p.lse[o] = mm + logf(sm);
-      }
+    }
+    if (total > 0) {
+      named_sync(kBarFW, FT);  // every pair of the last batch is reduced
+      merge_commit(ms, res + ((total - 1) & 1) * 3 * PAIRS);
     }
   }
 }

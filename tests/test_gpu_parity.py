@@ -78,6 +78,8 @@ CASES = [
     (128, 32, 12, 1, 37, 23),    # ragged image groups and template batches
     (256, 64, 12, 3, 7, 13),     # throughput geometry, 9 translations, ragged
     (256, 64, 12, 3, 2, 1),      # single template
+    (256, 64, 12, 3, 5, 4),      # one template batch, images spanning passes
+    (256, 64, 8, 3, 11, 6),      # H = 8: nine passes per image group, two template batches
     (256, 64, 64, 2, 3, 5),      # H = 64 (widest register block), 4 translations
     (256, 40, 20, 1, 9, 11),     # H padded to 24
     (512, 48, 16, 2, 5, 4),      # Q = 512
