@@ -204,6 +204,8 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
     // first (item i -> thread (i % warps) * 32 + i / warps)
     constexpr int FWARPS = FT / 32;
     const int my_item = (ftid % 32) * FWARPS + ftid / 32;
+    // at most (images touched by a pass) x TB items per batch; other threads skip the merge
+    const bool merger = my_item < ((RP + T - 1) / T + 1) * TB;
     struct MergeSlot {
       int it, item;
       bool active, rmw, fetched;
@@ -285,8 +287,10 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
       const int j0 = b * TB;
       const int nb = min(TB, N_B - j0);
       named_sync(kBarFull0 + (it & 1), CT + FT);
-      if (it > 0) merge_commit(ms, res + ((it - 1) & 1) * 3 * PAIRS);
-      ms = merge_prepare(it);
+      if (merger) {
+        if (it > 0) merge_commit(ms, res + ((it - 1) & 1) * 3 * PAIRS);
+        ms = merge_prepare(it);
+      }
       float* rs = res + (it & 1) * 3 * PAIRS;
       const float2* specb = spec + (size_t)(it & 1) * C::SPB * SP;
 #pragma unroll 1
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
     }
     if (total > 0) {
       named_sync(kBarFW, FT);  // every pair of the last batch is reduced
-      merge_commit(ms, res + ((total - 1) & 1) * 3 * PAIRS);
+      if (merger) merge_commit(ms, res + ((total - 1) & 1) * 3 * PAIRS);
     }
   }
 }
