@@ -200,10 +200,9 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
     const int ft = ftid % F;
     const float s2 = p.inv_sigma2;
     const float log2e = 1.44269504088896340736f;
-    // merge items of a batch: (image, template) pairs, spread one per warp lane 0
-    // first (item i -> thread (i % warps) * 32 + i / warps)
-    constexpr int FWARPS = FT / 32;
-    const int my_item = (ftid % 32) * FWARPS + ftid / 32;
+    // merge items of a batch ((image, template) pairs) live on the first FFT
+    // warp's lanes: only that warp pays their issue slots
+    const int my_item = ftid;
     // at most (images touched by a pass) x TB items per batch; other threads skip the merge
     const bool merger = my_item < ((RP + T - 1) / T + 1) * TB;
     struct MergeSlot {
