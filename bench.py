@@ -327,9 +327,10 @@ def run_ours(args):
     achieved = flops / (align_avg_ms / 1e3) / 1e12
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
-    roofline = {"bound": "alu", "kernel": "fused_align_kernel<128,12>", "achieved": round(achieved, 2),
+    kname = f"ws_align_kernel<{Q // 2},{12 if H <= 12 else 16}>" if (Q == 256 and H <= 16) else "fused_align_kernel"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": _load_traffic("fused_align_kernel<128,12>@throughput"),
+                "traffic": _load_traffic(kname + "@" + args.config) if args.n_images == 0 else None,
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
                 "align_ms": round(align_avg_ms, 3), "compress_ms": round(sum(compress_ms) / K, 3)}
 
