@@ -15,7 +15,7 @@
 //   write    slots s = 0 .. Q/2-1 of a_t(h, q) / Q, slot 0 packing (Re a(0), Re a(Q/2)).
 #include <math.h>
 
-#include "rsvd_internal.cuh"
+#include "compress_v2.cuh"
 
 namespace rsvd {
 namespace {
@@ -180,6 +180,33 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
   for (int t = 0; t < T; ++t) {
     p.dx[t] = deltas ? (float)deltas[2 * t] : 0.0f;
     p.dy[t] = deltas ? (float)deltas[2 * t + 1] : 0.0f;
+  }
+  {
+    // shared-memory kernel when half of one object's rings fits (compress_v2.cu)
+    Compress2Params q{};
+    q.polar = p.polar;
+    q.out = p.out;
+    q.U = U;
+    q.N = N;
+    q.R = R;
+    q.Q = Q;
+    q.H = H;
+    q.T = T;
+    bool uniform = k[0] > 0.0;
+    for (int r = 0; r < R && uniform; ++r) uniform = fabs(k[r] - (r + 1) * k[0]) <= 1e-9 * k[R - 1];
+    q.uniform = uniform ? 1 : 0;
+    q.dk = (float)k[0];
+    for (int r = 0; r < R; ++r) {
+      q.k[r] = p.k[r];
+      q.sw[r] = p.sw[r];
+    }
+    for (int t = 0; t < T; ++t) {
+      q.dx[t] = p.dx[t];
+      q.dy[t] = p.dy[t];
+    }
+    const int rc2 = (R * (Q / 2) * 8 <= 96 * 1024) ? launch_compress_v2(q, static_cast<cudaStream_t>(stream))
+                                                     : RSVD_EUNSUPPORTED;
+    if (rc2 != RSVD_EUNSUPPORTED) return rc2;
   }
   const int M = Q / 2;
   const int L = M < kThreads ? M : kThreads;

@@ -47,6 +47,22 @@ def test_compress_matches_oracle(Q, R, H, T_side):
     P.status()
 
 
+def test_compress_non_uniform_rings():
+    """Ring radii that are not equispaced (as from a Gauss-Jacobi rule) take the
+    per-ring phase evaluation instead of the ring-to-ring rotation."""
+    wl, A, B, U = setup(N=128, R=40, Q=256, N_B=2, N_A=3, T_side=3, H=12, seed=77)
+    g = wl.grid
+    rng = np.random.default_rng(3)
+    k = np.sort(rng.uniform(1.0, g.K, size=g.R))
+    w = rng.uniform(0.5, 2.0, size=g.R) * k
+    At = torch.from_numpy(A).to(DEV)
+    cA = P.compress(k, w, torch.from_numpy(U).to(DEV), At, deltas=wl.deltas).cpu().numpy()
+    a_c = O.compress(O.translate(A.astype(np.complex128), k, wl.deltas), U, w)
+    ref = pack_slots(a_c).reshape(3 * 9, 12, 128, 2)
+    scale = np.max(np.abs(ref), axis=(1, 2, 3), keepdims=True)
+    assert np.max(np.abs(cA - ref) / scale) < RTOL
+
+
 @pytest.mark.parametrize("H", [32, 8])
 def test_align_scores_tiny_workload(H):
     """64 images x 16 templates, 64x64 px, 32 rings, Q = 128, T = 1: full landscape."""
