@@ -19,13 +19,18 @@ from .rsvd_ref import (  # noqa: F401
     compress,
     compress_adjoint,
     fb_coefficients,
+    half_spectrum_operand,
     lse_loss,
     lse_grad_compressed,
     lse_loss_grad,
     lse_pair_partials,
+    operand_terms,
     principal_vectors,
     radial_kernel,
+    round_bf16,
+    round_fp16,
     scores_compressed,
+    scores_compressed_form,
     scores_direct,
     scores_fb,
     translate,

@@ -218,3 +218,69 @@ def compress_adjoint(G_c: np.ndarray, U: np.ndarray, w: np.ndarray, k: np.ndarra
     proj = deltas[:, 0][:, None] * np.cos(psi)[None, :] + deltas[:, 1][:, None] * np.sin(psi)[None, :]
     phase = np.exp(-1j * k[None, :, None] * proj[:, None, :])  # [T, R, Q]
     return np.einsum("ntrq,trq->nrq", G_Ft, np.conj(phase))
+
+
+# ---------------------------------------------------------------------------
+# Step 1 of eq. image_innerproduct_pm with reduced-precision operands. The
+# paper evaluates the contraction in full precision; these forms restate it
+# with the compressed coefficients rounded before the products (as tensor
+# cores take them), the products and sums exact:
+#   single  X_hat(q) = 2 pi sum_h conj(rn(a_h(q))) rn(b_h(q)),  rn = bf16 or fp16
+#   split   x = hi + lo, hi = rn_bf16(x), lo = rn_bf16(x - hi) (per real component);
+#           X_hat(q) = 2 pi sum_h [conj(a_hi) b_hi + conj(a_hi) b_lo + conj(a_lo) b_hi]
+#           (the compensated bf16x3 product of Henry, Tang & Heinecke,
+#           ARITH 2019; the lo*lo term is dropped).
+# Only the half spectrum q = 0..Q/2 is an operand (real images: the rest is
+# its conjugate), and the q = 0 and q = Q/2 coefficients enter by their real
+# parts.
+# ---------------------------------------------------------------------------
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 value (8 significant bits), ties to even,
+    for finite x in the normal range; returned as float64."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)  # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.round(np.ldexp(m, 8)), e - 8)  # np.round: half to even
+
+
+def round_fp16(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest IEEE binary16 value (ties to even, subnormals kept)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+def half_spectrum_operand(c: np.ndarray) -> np.ndarray:
+    """The operand a compressed ring contributes: q = 0..Q/2 with the imaginary
+    parts of q = 0 and q = Q/2 dropped, extended to q = Q/2+1..Q-1 by
+    conjugation. c [..., Q] complex -> [..., Q]."""
+    Q = c.shape[-1]
+    h = c[..., : Q // 2 + 1].copy()
+    h[..., 0] = h[..., 0].real
+    h[..., Q // 2] = h[..., Q // 2].real
+    return np.concatenate([h, np.conj(h[..., 1 : Q // 2][..., ::-1])], axis=-1)
+
+
+def _round_complex(z: np.ndarray, rn) -> np.ndarray:
+    return rn(z.real) + 1j * rn(z.imag)
+
+
+def operand_terms(a_c: np.ndarray, b_c: np.ndarray, form: str) -> list[tuple[np.ndarray, np.ndarray]]:
+    """The (image operand, template operand) pairs whose Step-1 products are
+    summed for `form` in {"fp64", "bf16", "fp16", "bf16x3"}."""
+    a = half_spectrum_operand(a_c)
+    b = half_spectrum_operand(b_c)
+    if form == "fp64":
+        return [(a, b)]
+    if form in ("bf16", "fp16"):
+        rn = round_bf16 if form == "bf16" else round_fp16
+        return [(_round_complex(a, rn), _round_complex(b, rn))]
+    if form == "bf16x3":
+        a_hi, b_hi = _round_complex(a, round_bf16), _round_complex(b, round_bf16)
+        a_lo, b_lo = _round_complex(a - a_hi, round_bf16), _round_complex(b - b_hi, round_bf16)
+        return [(a_hi, b_hi), (a_hi, b_lo), (a_lo, b_hi)]
+    raise ValueError(form)
+
+
+def scores_compressed_form(a_c: np.ndarray, b_c: np.ndarray, form: str) -> np.ndarray:
+    """Real X [nA, T, nB, Q] of eq. image_innerproduct_pm with the operands of
+    `form`: X_hat = 2 pi sum over terms of sum_h conj(A) B, X = forward DFT."""
+    Xhat = sum(2.0 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(A), B) for A, B in operand_terms(a_c, b_c, form))
+    return np.fft.fft(Xhat, axis=-1).real

@@ -1,0 +1,112 @@
+"""Pins of the oracle's reduced-precision operand forms (the Step-1 contraction
+of eq. image_innerproduct_pm with bf16 / fp16 / split-bf16x3 operands) to
+things other than the oracle itself: library conversions, representability,
+error bounds of the rounding, and the exact case."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synthetic import make_workload
+
+
+def _scale_mix(rng, n):
+    return rng.standard_normal(n) * np.exp(rng.uniform(-12, 6, n))
+
+
+def test_round_bf16_matches_torch_conversion_on_float32_inputs():
+    rng = np.random.default_rng(0)
+    x = _scale_mix(rng, 20000).astype(np.float32)
+    # exact ties between two bfloat16 neighbours, even and odd kept bit
+    u = (rng.integers(0x3F000000, 0x42000000, 4000, dtype=np.uint32) & 0xFFFF0000) | 0x8000
+    x = np.concatenate([x, u.view(np.float32), -u.view(np.float32)])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(O.round_bf16(x), ref)
+
+
+def test_round_bf16_is_nearest_with_eight_significant_bits():
+    rng = np.random.default_rng(1)
+    x = _scale_mix(rng, 5000)
+    r = O.round_bf16(x)
+    m, e = np.frexp(r)
+    assert np.array_equal(np.ldexp(m, 8), np.round(np.ldexp(m, 8)))  # 8 significant bits
+    _, ex = np.frexp(x)
+    ulp = np.ldexp(1.0, ex - 8)
+    assert np.all(np.abs(x - r) <= ulp / 2)
+    assert np.all(np.abs(r) <= np.abs(x) * (1 + 2.0**-8))
+
+
+def test_round_fp16_matches_torch_conversion():
+    rng = np.random.default_rng(2)
+    x = (rng.standard_normal(20000) * np.exp(rng.uniform(-18, 8, 20000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.float16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(O.round_fp16(x), ref)
+
+
+def test_split_represents_value_to_sixteen_bits():
+    rng = np.random.default_rng(3)
+    x = _scale_mix(rng, 5000)
+    hi = O.round_bf16(x)
+    lo = O.round_bf16(x - hi)
+    assert np.all(np.abs(lo) <= 2.0**-8 * np.abs(x) * (1 + 2.0**-7))
+    assert np.all(np.abs(x - hi - lo) <= 2.0**-16 * np.abs(x))
+
+
+def test_half_spectrum_operand_is_hermitian_with_real_ends():
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal((3, 5, 32)) + 1j * rng.standard_normal((3, 5, 32))
+    h = O.half_spectrum_operand(c)
+    assert np.all(h[..., 0].imag == 0) and np.all(h[..., 16].imag == 0)
+    assert np.array_equal(h[..., 1:16], c[..., 1:16])
+    assert np.array_equal(h[..., 17:], np.conj(h[..., 1:16][..., ::-1]))
+
+
+def _small():
+    wl = make_workload(N=32, R=16, Q=32, N_B=5, N_A=6, snr=0.2, T_side=2, seed=21)
+    g = wl.grid
+    U, _ = O.principal_vectors(O.radial_kernel(wl.templates, g.w), 8)
+    a = O.compress(O.translate(wl.images, g.k, wl.deltas), U, g.w)
+    b = O.compress(wl.templates, U, g.w)
+    return a, b
+
+
+def test_forms_reduce_to_the_exact_score_on_representable_operands():
+    a, b = _small()
+    rb = lambda z: O.round_bf16(z.real) + 1j * O.round_bf16(z.imag)
+    a16, b16 = rb(O.half_spectrum_operand(a)), rb(O.half_spectrum_operand(b))
+    X = O.scores_compressed(a16, b16).real
+    for form in ("bf16", "bf16x3", "fp64"):
+        Xf = O.scores_compressed_form(a16, b16, form)
+        assert np.allclose(Xf, X, rtol=0, atol=1e-13 * np.abs(X).max()), form
+    rh = lambda z: O.round_fp16(z.real) + 1j * O.round_fp16(z.imag)
+    ah, bh = rh(O.half_spectrum_operand(a)), rh(O.half_spectrum_operand(b))
+    Xh = O.scores_compressed(ah, bh).real
+    assert np.allclose(O.scores_compressed_form(ah, bh, "fp16"), Xh, rtol=0, atol=1e-13 * np.abs(Xh).max())
+
+
+def test_fp64_form_of_real_image_rings_is_the_plain_score():
+    a, b = _small()
+    X = O.scores_compressed(a, b).real
+    assert np.allclose(O.scores_compressed_form(a, b, "fp64"), X, rtol=0, atol=1e-12 * np.abs(X).max())
+
+
+def test_form_errors_follow_the_rounding_bounds():
+    """bf16x3 keeps about 16 significand bits: relative error far below the
+    single-pass forms, and dropping any one of its three terms is visible."""
+    a, b = _small()
+    X = O.scores_compressed(a, b).real
+    nrm = np.linalg.norm(X)
+    err = {f: np.linalg.norm(O.scores_compressed_form(a, b, f) - X) / nrm for f in ("bf16", "fp16", "bf16x3")}
+    assert 1e-4 < err["bf16"] < 1e-2
+    assert 1e-5 < err["fp16"] < 2e-3
+    assert err["bf16x3"] < 1e-5
+    assert err["bf16x3"] < err["fp16"] / 10
+    terms = O.operand_terms(a, b, "bf16x3")
+    for drop in range(3):
+        kept = [t for i, t in enumerate(terms) if i != drop]
+        Xhat = sum(2 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(A), B) for A, B in kept)
+        e = np.linalg.norm(np.fft.fft(Xhat, axis=-1).real - X) / nrm
+        assert e > 10 * err["bf16x3"], drop
