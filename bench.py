@@ -217,8 +217,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     precompute_ms = e0.elapsed_time(e1)
 
-    cA = torch.empty((N_A * T, H, Q // 2, 2), dtype=torch.float32, device=dev)
-    cB = torch.empty((N_B, H, Q // 2, 2), dtype=torch.float32, device=dev)
+    prec = args.precision
+    if prec == "fp32":
+        cA = torch.empty((N_A * T, H, Q // 2, 2), dtype=torch.float32, device=dev)
+        cB = torch.empty((N_B, H, Q // 2, 2), dtype=torch.float32, device=dev)
+    else:  # tensor-core operand form (byte tensors)
+        cA = torch.empty((P.compressed_bytes(N_A, T, H, Q, prec),), dtype=torch.uint8, device=dev)
+        cB = torch.empty((P.compressed_bytes(N_B, 1, H, Q, prec),), dtype=torch.uint8, device=dev)
     best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
     arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
@@ -230,11 +235,11 @@ def run_ours(args):
     def step(i=None):
         if i is not None:
             ev_c0[i].record(stream)
-        P.compress(grid.k, grid.w, U, imgs, deltas=deltas, out=cA)
-        P.compress(grid.k, grid.w, U, tmpl, out=cB)
+        P.compress(grid.k, grid.w, U, imgs, deltas=deltas, out=cA, precision=prec)
+        P.compress(grid.k, grid.w, U, tmpl, out=cB, precision=prec)
         if i is not None:
             ev_a0[i].record(stream)
-        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None))
+        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None), precision=prec)
         if i is not None:
             ev_a1[i].record(stream)
 
@@ -295,9 +300,9 @@ def run_ours(args):
     def e2e_step():
         imgs_d.copy_(imgs_h, non_blocking=True)
         tmpl_d.copy_(tmpl_h, non_blocking=True)
-        P.compress(grid.k, grid.w, U, imgs_d, deltas=deltas, out=cA)
-        P.compress(grid.k, grid.w, U, tmpl_d, out=cB)
-        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None))
+        P.compress(grid.k, grid.w, U, imgs_d, deltas=deltas, out=cA, precision=prec)
+        P.compress(grid.k, grid.w, U, tmpl_d, out=cB, precision=prec)
+        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None), precision=prec)
         best_h.copy_(best, non_blocking=True)
         arg_h.copy_(arg, non_blocking=True)
 
@@ -542,6 +547,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="throughput")
     ap.add_argument("--n-images", type=int, default=0, help="override images per GPU (smaller runs)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
+                    help="operand precision of the scoring contraction (tensor cores unless fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-images", type=int, default=0, help="images in the cpu_baseline sample (0 = auto)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target wall time of the cpu_baseline sample")

@@ -51,8 +51,22 @@ enum rsvd_status_code {
   RSVD_ENOCONVERGE = -7    /* eigen-solver sweep limit reached (status word)    */
 };
 
-/* Operand precision of the compressed rings. Only RSVD_FP32 is implemented in
- * this version; the others return RSVD_EUNSUPPORTED. */
+/* Operand precision of the compressed rings (the Step-1 contraction of
+ * eq. image_innerproduct_pm, X_hat(q) = 2 pi sum_h conj(a_h(q)) b_h(q)):
+ *   RSVD_FP32    FP32 coefficients, FP32 arithmetic (CUDA cores)
+ *   RSVD_BF16    coefficients rounded to bfloat16, products summed in FP32 on
+ *                the tensor cores (single pass)
+ *   RSVD_FP16    the same with IEEE half precision (single pass; coefficients
+ *                below 2^-14 lose precision in the half-precision subnormal range)
+ *   RSVD_BF16X3  each FP32 coefficient x split as hi = rn_bf16(x),
+ *                lo = rn_bf16(x - hi); the products a_hi b_hi + a_hi b_lo + a_lo b_hi
+ *                summed in FP32 on the tensor cores (about 16 significand bits)
+ * Step 2 (the transform over q) and the reductions run in FP32 for every form.
+ * The three tensor-core forms support Q in {128, 256}, H <= 32, T <= 64
+ * (else RSVD_EUNSUPPORTED) in rsvd_compress (shared-memory compression kernel:
+ * R * Q <= 24576), rsvd_pack, rsvd_align_scores and rsvd_align_best; scoring
+ * with RSVD_BF16X3 at Q = 256 takes H <= 18 (shared memory). The gradient
+ * entry points take RSVD_FP32 only. */
 enum rsvd_precision { RSVD_FP32 = 0, RSVD_BF16 = 1, RSVD_FP16 = 2, RSVD_BF16X3 = 3 };
 
 /* RSVD_ABI_VERSION of the loaded library. */
@@ -135,11 +149,31 @@ int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, const void* tem
  * element [row][h][s] at offset ((row*H + h)*(Q/2) + s)*8 bytes, where slot
  * s >= 1 is a_t(h, s) and slot 0 packs the two real coefficients
  * (Re a_t(h, 0), Re a_t(h, Q/2)).
+ *
+ * Layout of `out` for RSVD_BF16 / RSVD_FP16 / RSVD_BF16X3 (the tensor-core
+ * operand form): one plane of 16-bit floats (BF16X3: a hi plane, then a lo
+ * plane of the same size). With g = Q/64 slots per group, Hp = H rounded up so
+ * that K = 2*Hp*g is a multiple of 16, IPT = 128/T objects per tile and
+ * tiles = ceil(N/IPT), a plane is the array
+ *   [tiles][32 groups][K/8][128 lanes][8]
+ * where component (re: c = 0, im: c = 1) of (object n, translation t, vector h,
+ * slot s) sits at group s % 32, k = (s / 32)*2*Hp + 2*h + c, lane (n % IPT)*T + t
+ * of tile n / IPT; every other element is zero. Each [tile][group] block is
+ * the 128 x K K-major operand image of one tensor-core contraction.
+ * rsvd_compressed_bytes returns 0 for a size or precision outside these limits.
  * ------------------------------------------------------------------------ */
 size_t rsvd_compressed_bytes(int N, int T, int H, int Q, int precision);
 int rsvd_compress(int R, int Q, const double* k, const double* w, const double* U, int H,
                   const void* polar, int N, const double* deltas, int T, int precision, void* out,
                   void* stream);
+
+/* Converts compressed rings written with RSVD_FP32 (N objects, T translations)
+ * into the operand form of `precision` (RSVD_BF16, RSVD_FP16 or RSVD_BF16X3),
+ * rounding each FP32 component to nearest (ties to even). The result equals
+ * rsvd_compress called with that precision on the same input, byte for byte.
+ *   c32  dev, rsvd_compressed_bytes(N, T, H, Q, RSVD_FP32) bytes, 8-byte aligned
+ *   out  dev, rsvd_compressed_bytes(N, T, H, Q, precision) bytes, 16-byte aligned */
+int rsvd_pack(const void* c32, int N, int T, int H, int Q, int precision, void* out, void* stream);
 
 /* ------------------------------------------------------------------------
  * Full score array (small problems). Eq. (image_innerproduct_pm):
@@ -149,6 +183,7 @@ int rsvd_compress(int R, int Q, const double* k, const double* w, const double* 
  *
  *   cA   dev compressed images, N_A objects x T translations (rsvd_compress)
  *   cB   dev compressed templates, N_B objects, T = 1
+ *        (both in the layout of `precision`; see rsvd_precision for the forms)
  *   X    dev float [N_A][T][N_B][Q] -- output; X[n][t][j][m] = X(gamma_m) for
  *        image n translated by delta_t against template j
  * ------------------------------------------------------------------------ */

@@ -2,12 +2,13 @@
 
 The compute path is librsvd.so (hand-written CUDA, C ABI in include/rsvd.h);
 this package is the thin Python binding: ``build_radial_svd``, ``compress``,
-``align_scores``, ``align_best``, ``status``.
+``pack``, ``align_scores``, ``align_best``, ``status``.
 """
 
 from ._native import RSVDError, lib, lib_path  # noqa: F401
 from .api import (  # noqa: F401
     FP32,
+    PRECISIONS,
     LSEAlign,
     align_best,
     align_scores,
@@ -20,5 +21,6 @@ from .api import (  # noqa: F401
     lse_align,
     lse_backward,
     lse_rows,
+    pack,
     status,
 )

@@ -43,6 +43,7 @@ SIGNATURES = {
                                        c_double_p, c_int, c_int, c_void_p, c_void_p]),
     "rsvd_align_best_pairwise": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float,
                                          c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rsvd_pack": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
 }
 
 

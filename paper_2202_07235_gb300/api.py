@@ -17,6 +17,15 @@ FP32 = 0
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
 
 
+def _prec(precision) -> int:
+    """Precision code from a name ("fp32", "bf16", "fp16", "bf16x3") or a code."""
+    if isinstance(precision, str):
+        return PRECISIONS[precision]
+    if int(precision) not in PRECISIONS.values():
+        raise ValueError(f"unknown precision {precision}")
+    return int(precision)
+
+
 def _stream(stream=None) -> int:
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(s.cuda_stream)
@@ -80,14 +89,24 @@ def build_radial_svd_noalloc(w, templates: torch.Tensor, H: int, stream=None):
     return U, eig
 
 
-def compressed_bytes(N: int, T: int, H: int, Q: int, precision: int = FP32) -> int:
-    return int(lib().rsvd_compressed_bytes(N, T, H, Q, precision))
+def compressed_bytes(N: int, T: int, H: int, Q: int, precision=FP32) -> int:
+    return int(lib().rsvd_compressed_bytes(N, T, H, Q, _prec(precision)))
+
+
+def _operand_buffer(N: int, T: int, H: int, Q: int, precision: int, device) -> torch.Tensor:
+    nbytes = compressed_bytes(N, T, H, Q, precision)
+    if nbytes == 0:
+        raise ValueError(f"no operand form for N={N}, T={T}, H={H}, Q={Q}, precision={precision}")
+    return torch.empty((nbytes,), dtype=torch.uint8, device=device)
 
 
 def compress(k, w, U: torch.Tensor, polar: torch.Tensor, deltas=None, precision: int = FP32,
              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Compressed rings. polar: complex64 [N, R, Q]; deltas: host (T, 2) or None.
-    Returns float32 [N*T, H, Q/2, 2] (complex slots; slot 0 packs q = 0 and q = Q/2)."""
+    Returns float32 [N*T, H, Q/2, 2] (complex slots; slot 0 packs q = 0 and q = Q/2)
+    for precision "fp32", else the tensor-core operand form as a uint8 byte
+    tensor (layout in include/rsvd.h)."""
+    precision = _prec(precision)
     _require_cuda(polar, torch.complex64, "polar")
     _require_cuda(U, torch.float64, "U")
     N, R, Q = polar.shape
@@ -100,15 +119,31 @@ def compress(k, w, U: torch.Tensor, polar: torch.Tensor, deltas=None, precision:
         da, dp = _host_f64(deltas)
         T = da.reshape(-1, 2).shape[0]
     if out is None:
-        out = torch.empty((N * T, H, Q // 2, 2), dtype=torch.float32, device=polar.device)
+        if precision == FP32:
+            out = torch.empty((N * T, H, Q // 2, 2), dtype=torch.float32, device=polar.device)
+        else:
+            out = _operand_buffer(N, T, H, Q, precision, polar.device)
     check(lib().rsvd_compress(R, Q, kp, wp, _ptr(U), H, _ptr(polar), N, dp, T, precision, _ptr(out),
                               _stream(stream)), "rsvd_compress")
     return out
 
 
+def pack(c32: torch.Tensor, N: int, T: int, H: int, Q: int, precision, out: torch.Tensor | None = None,
+         stream=None) -> torch.Tensor:
+    """FP32 compressed rings (N objects x T translations) -> operand form of
+    `precision` (byte tensor), rounded to nearest."""
+    precision = _prec(precision)
+    _require_cuda(c32, torch.float32, "c32")
+    if out is None:
+        out = _operand_buffer(N, T, H, Q, precision, c32.device)
+    check(lib().rsvd_pack(_ptr(c32), N, T, H, Q, precision, _ptr(out), _stream(stream)), "rsvd_pack")
+    return out
+
+
 def align_scores(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int,
-                 precision: int = FP32, stream=None) -> torch.Tensor:
+                 precision=FP32, stream=None) -> torch.Tensor:
     """Full landscape X float32 [N_A, T, N_B, Q]."""
+    precision = _prec(precision)
     X = torch.empty((N_A, T, N_B, Q), dtype=torch.float32, device=cA.device)
     check(lib().rsvd_align_scores(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, _ptr(X), _stream(stream)),
           "rsvd_align_scores")
@@ -116,9 +151,10 @@ def align_scores(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int,
 
 
 def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int,
-               inv_sigma2: float = 1.0, want_lse: bool = False, precision: int = FP32, out=None, stream=None,
+               inv_sigma2: float = 1.0, want_lse: bool = False, precision=FP32, out=None, stream=None,
                pairwise: bool = False):
     """best float32 [N_A, N_B], arg int32 [N_A, N_B] (t*Q+m), lse float32 or None."""
+    precision = _prec(precision)
     dev = cA.device
     if out is None:
         best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)

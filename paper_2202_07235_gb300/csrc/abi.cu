@@ -2,7 +2,7 @@
 // buffer-size queries.
 #include <mutex>
 
-#include "rsvd_internal.cuh"
+#include "operand.cuh"
 
 namespace rsvd {
 
@@ -63,8 +63,11 @@ int rsvd_status(void* stream) {
 }
 
 size_t rsvd_compressed_bytes(int N, int T, int H, int Q, int precision) {
-  if (N <= 0 || T <= 0 || H <= 0 || Q <= 0 || precision != RSVD_FP32) return 0;
-  return (size_t)N * (size_t)T * (size_t)H * (size_t)(Q / 2) * 8u;
+  if (N <= 0 || T <= 0 || H <= 0 || Q <= 0) return 0;
+  if (precision == RSVD_FP32) return (size_t)N * (size_t)T * (size_t)H * (size_t)(Q / 2) * 8u;
+  rsvd::OperandLayout L{};
+  if (!rsvd::is_operand_precision(precision) || !rsvd::make_operand_layout(N, T, H, Q, &L)) return 0;
+  return (size_t)rsvd::operand_planes(precision) * (size_t)L.plane_elems * 2u;
 }
 
 }  // extern "C"

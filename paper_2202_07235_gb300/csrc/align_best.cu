@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "align_ws.cuh"
+#include "operand.cuh"
 
 namespace rsvd {
 namespace {
@@ -23,6 +24,14 @@ int padded_h(int H) {
 extern "C" int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
                                float inv_sigma2, float* best, int32_t* arg, float* lse, void* stream) {
   using namespace rsvd;
+  if (precision != RSVD_FP32) {
+    int rc = check_tc_args(cA, N_A, T, cB, N_B, H, Q, precision);
+    if (rc != RSVD_OK) return rc;
+    if (!best || !arg) return RSVD_EINVAL;
+    if (lse && !(inv_sigma2 > 0.0f && isfinite(inv_sigma2))) return RSVD_EINVAL;
+    return align_tc(cA, N_A, T, cB, N_B, H, Q, precision, inv_sigma2, best, arg, lse, nullptr,
+                    static_cast<cudaStream_t>(stream));
+  }
   int rc = check_align_args(cA, N_A, T, cB, N_B, H, Q, precision);
   if (rc != RSVD_OK) return rc;
   if (!best || !arg) return RSVD_EINVAL;

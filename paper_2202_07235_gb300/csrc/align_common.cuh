@@ -18,6 +18,18 @@ inline int check_align_args(const void* cA, int N_A, int T, const void* cB, int 
   return RSVD_OK;
 }
 
+// Arguments of the tensor-core path (operand forms, operand.cuh): Q in
+// {128, 256}, H <= 32, T <= 64, operand planes 16-byte aligned.
+inline int check_tc_args(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision) {
+  if (!cA || !cB) return RSVD_EINVAL;
+  if (N_A <= 0 || N_B <= 0 || T <= 0 || H <= 0 || Q <= 0) return RSVD_EINVAL;
+  if (precision != RSVD_BF16 && precision != RSVD_FP16 && precision != RSVD_BF16X3) return RSVD_EUNSUPPORTED;
+  if (!(Q == 128 || Q == 256) || H > 32 || T > kMaxT) return RSVD_EUNSUPPORTED;
+  if (((uintptr_t)cA & 15u) || ((uintptr_t)cB & 15u)) return RSVD_EINVAL;
+  if ((long long)N_A * T > 0x7fffffffLL / 2) return RSVD_EUNSUPPORTED;
+  return RSVD_OK;
+}
+
 // Running log-sum-exp state (m, s): the represented value is m + log(s).
 __device__ __forceinline__ void lse_push(float& m, float& s, float v) {
   if (v > m) {
@@ -104,6 +116,10 @@ __device__ __forceinline__ float tree_sum(float (&v)[N]) {
     for (int i = 0; i < N; i += 2 * w) v[i] += v[i + w];
   return v[0];
 }
+
+// Tensor-core path for the operand forms (align_tc.cu): best/arg/lse, or X when X != NULL.
+RSVD_HIDDEN int align_tc(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
+                         float inv_sigma2, float* best, int32_t* arg, float* lse, float* X, cudaStream_t stream);
 
 // Generic per-pair path (align_pair.cu).
 RSVD_HIDDEN int align_best_pairwise(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,

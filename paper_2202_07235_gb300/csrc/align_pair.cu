@@ -211,6 +211,13 @@ RSVD_HIDDEN int align_best_pairwise(const void* cA, int N_A, int T, const void* 
 extern "C" int rsvd_align_scores(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
                                  float* X, void* stream) {
   using namespace rsvd;
+  if (precision != RSVD_FP32) {
+    int rc = check_tc_args(cA, N_A, T, cB, N_B, H, Q, precision);
+    if (rc != RSVD_OK) return rc;
+    if (!X) return RSVD_EINVAL;
+    return align_tc(cA, N_A, T, cB, N_B, H, Q, precision, 0.0f, nullptr, nullptr, nullptr, X,
+                    static_cast<cudaStream_t>(stream));
+  }
   int rc = check_align_args(cA, N_A, T, cB, N_B, H, Q, precision);
   if (rc != RSVD_OK) return rc;
   if (!X) return RSVD_EINVAL;

@@ -1,0 +1,603 @@
+// Tensor-core scoring for the reduced-precision operand forms (operand.cuh):
+// rsvd_align_best and rsvd_align_scores with RSVD_BF16, RSVD_FP16, RSVD_BF16X3.
+//
+// Eq. (image_innerproduct_pm):
+//   Step 1  X_hat(q) = 2 pi sum_h conj(a_h(q)) b_h(q)      -> tcgen05.mma into TMEM
+//   Step 2  X(gamma_m) = sum_q e^{-i q gamma_m} X_hat(q)   -> per-thread FFT read from TMEM
+// followed by the max / argmax / log-sum-exp over (gamma, delta) of
+// sections 2.6-2.7, or the full X.
+//
+// Work item: a tile of 128 image rows (objects x translations, operand.cuh)
+// against NT = 512 / Q templates. TMEM (128 lanes x 512 FP32 columns) holds the
+// whole half spectrum of the 128 x NT pairs: lane = image row, column =
+// 16 * group + (template, slot in group, re/im).
+//
+// Step 1 as real products of (re, im) components. For each of the 32 slot
+// groups, one MMA chain D[128 x 16] += A[128 x K] * B[16 x K]^T with
+//   A row    = the image row's components of the group's g slots (k = u 2Hp + 2h + c),
+//   B row    = (template jj, slot u, c_out): zero outside the K range of slot u,
+//              (b_re, b_im) for c_out = re and (b_im, -b_re) for c_out = im
+//              (slot 0: (b(0), 0) and (0, b(Q/2)), the two real terms),
+// so D(row, (jj, u, re)) = Re sum_h conj(a) b and D(.., im) = Im sum_h conj(a) b.
+// The block-diagonal B is built in shared memory by the producer warp from the
+// template rows; A arrives by bulk copy (TMA) of the row tile's operand block.
+// Split-bf16x3 accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi in the same
+// FP32 accumulator.
+//
+// Step 2 (per thread = one (image row, template) pair, reading only its own
+// TMEM lane): the real Q-point transform of the half spectrum as a complex
+// M = Q/2 point DFT of
+//   Z(k) = [X_hat(k) + conj X_hat(M - k)] + i W_Q^k [X_hat(k) - conj X_hat(M - k)],
+//   z(p) = sum_k Z(k) W_M^{kp} = X(2p) + i X(2p + 1),
+// split as M = g x 32 with k = k1 + 32 u, p = p1 + g p2: group k1 of TMEM holds
+// exactly the g inputs k1 + 32 u of one first-stage DFT (and pairs with group
+// 32 - k1 for the conjugate terms); first-stage results (twiddled by
+// W_M^{k1 p1}) go back to the same columns, then each second-stage 32-point DFT
+// gathers column 2 p1 of every group.
+//
+// Roles: warps 0 and 10 producers (alternate groups, one template-row copy
+// each), warp 1 TMEM allocation + MMA issue (one elected lane of the converged
+// warp), warps 2..9 epilogue (two warps per TMEM lane quadrant). Every wait is
+// bounded (status word + abort flag; no role can hang the others).
+#include <math.h>
+
+#include "align_common.cuh"
+#include "operand.cuh"
+#include "tc_ptx.cuh"
+
+namespace rsvd {
+namespace {
+
+constexpr int kTcThreads = 352;  // warps 0, 10 producers; 1 MMA; 2..9 epilogue
+constexpr int kEpiThreads = 256;
+constexpr long long kTcBudget = 1LL << 31;  // clock cycles per bounded wait
+constexpr int kBarEpi = 1;
+constexpr int kTmemCols = 512;
+
+template <int Q>
+struct TcCfg {
+  static constexpr int M = Q / 2;      // points of the half-length DFT (= packed slots)
+  static constexpr int g = Q / 64;     // slots per group
+  static constexpr int NT = 512 / Q;   // templates per tile
+  static constexpr int TPT = NT / 2;   // templates per epilogue thread
+};
+
+struct TcParams {
+  const uint16_t* a;  // image operand planes (hi, then lo)
+  const uint16_t* b;  // template operand planes
+  long long a_plane, b_plane;
+  float* best;
+  int32_t* arg;
+  float* lse;
+  float* X;
+  int* status;
+  int N_A, T, N_B, IPT, nRT, nTP, CH, nUnits;
+  int K, KC, KS, Hp, stages, split, lse_on, nprod;
+  float inv_sigma2;
+  uint32_t idesc;
+  uint32_t stage_bytes, a_bytes, b_bytes, dense_off, dense_bytes, res_off, bar_off;
+  float2 WQ[128];  // W_Q^k = exp(-2 pi i k / Q), k < Q/2
+  float2 WM[128];  // W_M^k, M = Q/2
+};
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                        int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kTcBudget) {
+      record(status, kDevTimeout);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Z(k) = [X + conj P] + i w [X - conj P]
+__device__ __forceinline__ float2 zform(float2 X, float2 P, float2 w) {
+  const float2 A = make_float2(X.x + P.x, X.y - P.y);
+  const float2 B = make_float2(X.x - P.x, X.y + P.y);
+  const float2 C = cmul(w, B);
+  return make_float2(A.x - C.y, A.y + C.x);
+}
+
+// Step 2 and the per-row reduction for one (image row, template jj) pair.
+// Returns (max of X / 2pi over m, its m, lse max, lse sum) with the lse in units
+// of inv_sigma2 * X; writes X instead when kWriteX.
+template <int Q, bool kWriteX>
+__device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj, bool row_ok, float* xrow) {
+  using C = TcCfg<Q>;
+  constexpr int g = C::g;
+  const uint32_t cb = (uint32_t)(jj * 2 * g);
+
+  // ---- first stage: pre-processing, g-point DFTs, twiddles; in place ----
+#pragma unroll
+  for (int k1 = 0; k1 <= 16; ++k1) {
+    const int k2 = (32 - k1) & 31;
+    float2 xa[g], xb[g], za[g], zb[g];
+    tmem_ld_pair<g>(tl + k1 * 16 + cb, tl + k2 * 16 + cb, xa, xb);
+    if (k1 == 0) {
+      za[0] = make_float2(xa[0].x + xa[0].y, xa[0].x - xa[0].y);  // X_hat(0), X_hat(M) real
+#pragma unroll
+      for (int u = 1; u < g; ++u) za[u] = zform(xa[u], xa[g - u], p.WQ[32 * u]);
+    } else if (k1 == 16) {
+#pragma unroll
+      for (int u = 0; u < g; ++u) za[u] = zform(xa[u], xa[g - 1 - u], p.WQ[16 + 32 * u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < g; ++u) {
+        const float2 X = xa[u], P = xb[g - 1 - u];
+        const float2 A = make_float2(X.x + P.x, X.y - P.y);
+        const float2 B = make_float2(X.x - P.x, X.y + P.y);
+        const float2 Cw = cmul(p.WQ[k1 + 32 * u], B);
+        za[u] = make_float2(A.x - Cw.y, A.y + Cw.x);          // A + i C
+        zb[g - 1 - u] = make_float2(A.x + Cw.y, Cw.x - A.y);  // conj(A) + i conj(C): k' = M - k
+      }
+    }
+    RegDft<g>::run(za);
+#pragma unroll
+    for (int p1 = 1; p1 < g; ++p1) za[p1] = cmul(za[p1], p.WM[k1 * p1]);
+    tmem_st<g>(tl + k1 * 16 + cb, za);
+    if (k2 != k1) {
+      RegDft<g>::run(zb);
+#pragma unroll
+      for (int p1 = 1; p1 < g; ++p1) zb[p1] = cmul(zb[p1], p.WM[k2 * p1]);
+      tmem_st<g>(tl + k2 * 16 + cb, zb);
+    }
+  }
+  tmem_wait_st();
+
+  // ---- second stage: 32-point DFTs over k1, reductions ----
+  constexpr float kTwoPi = 6.283185307179586f;
+  const float cs = kTwoPi * p.inv_sigma2;
+  float best = -INFINITY, lm = -INFINITY, ls = 0.0f;
+  int bm = 0;
+#pragma unroll
+  for (int p1 = 0; p1 < g; ++p1) {
+    float2 z[32];
+#pragma unroll
+    for (int b8 = 0; b8 < 4; ++b8) {
+      float2 w8[8];
+      tmem_ld2x8(tl + (uint32_t)(b8 * 8 * 16) + cb + 2 * p1, 16, w8);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) z[b8 * 8 + i] = w8[i];
+    }
+    RegDft<32>::run(z);  // z[p2] = X(2p) + i X(2p+1) over 2 pi, p = p1 + g p2
+    if (kWriteX) {
+      if (row_ok) {
+#pragma unroll
+        for (int p2 = 0; p2 < 32; ++p2)
+          *reinterpret_cast<float2*>(xrow + 2 * (p1 + g * p2)) = make_float2(kTwoPi * z[p2].x, kTwoPi * z[p2].y);
+      }
+    } else {
+      float v[64];
+#pragma unroll
+      for (int p2 = 0; p2 < 32; ++p2) {
+        v[2 * p2] = z[p2].x;
+        v[2 * p2 + 1] = z[p2].y;
+      }
+      float pb;
+      int pi;
+      tree_argmax<64>(v, pb, pi);  // m increases with the index within a pass
+      const int m = 2 * p1 + 2 * g * (pi >> 1) + (pi & 1);
+      if (pb > best || (pb == best && m < bm)) {
+        best = pb;
+        bm = m;
+      }
+      if (p.lse_on) {
+        const float off = pb * cs;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 64; ++i) acc[i & 3] += __expf(fmaf(v[i], cs, -off));
+        lse_merge(lm, ls, off, (acc[0] + acc[1]) + (acc[2] + acc[3]));
+      }
+    }
+  }
+  return make_float4(best, __int_as_float(bm), lm, ls);
+}
+
+template <int Q, bool kWriteX>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_constant__ TcParams p) {
+  using C = TcCfg<Q>;
+  constexpr int g = C::g, NT = C::NT, TPT = C::TPT;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + p.bar_off);
+  uint64_t* empty = full + p.stages;
+  uint64_t* tmem_full = empty + p.stages;
+  uint64_t* tmem_empty = tmem_full + 1;
+  uint64_t* drain = tmem_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile uint32_t* abort_flag = tmem_slot + 1;
+  // template rows [plane][jj][group][K], one copy per producer warp
+  uint16_t* dense = reinterpret_cast<uint16_t*>(tc_smem + p.dense_off + (threadIdx.x >= 320 ? p.dense_bytes : 0u));
+  float4* res = reinterpret_cast<float4*>(tc_smem + p.res_off);          // [2][NT][128]
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int planes = p.split ? 2 : 1;
+
+  if (tid == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 2);  // expect_tx arrival + arrival after the template block is written
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tmem_full, 1);
+    mbar_init(tmem_empty, kEpiThreads);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  // the template blocks' zeros never change: clear them once
+  for (int s = 0; s < p.stages; ++s) {
+    uint32_t* bz = reinterpret_cast<uint32_t*>(tc_smem + (size_t)s * p.stage_bytes + planes * p.a_bytes);
+    for (int i = tid; i < (int)(planes * p.b_bytes / 4); i += kTcThreads) bz[i] = 0u;
+  }
+  fence_proxy_async_smem();
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 || (warp == 10 && p.nprod == 2)) {
+    // ================= producers =================
+    const long long mine = warp == 10 ? 1 : 0;  // with two producers, this warp fills the groups with it % 2 == mine
+    // This lane's entries of the block-diagonal template operand, the same for
+    // every group: source word in the template rows (group 0, plane 0),
+    // destination word in the block, slot-0 flag (u == 0).
+    constexpr int kMaxItems = 8;  // NT * g * Hp / 32 with Hp <= 32
+    int it_src[kMaxItems], it_dst[kMaxItems];
+    uint32_t it_u0 = 0u;
+    const int n_items = NT * g * p.Hp;
+#pragma unroll
+    for (int r = 0; r < kMaxItems; ++r) {
+      const int i = lane + 32 * r;
+      it_src[r] = -1;
+      it_dst[r] = 0;
+      if (i < n_items) {
+        const int h = i % p.Hp;
+        const int q = i / p.Hp;
+        const int u = q % g, jj = q / g;
+        const int k = u * 2 * p.Hp + 2 * h;
+        const int nr = jj * 2 * g + 2 * u;
+        it_src[r] = (jj * kOpGroups * p.K + k) >> 1;
+        it_dst[r] = ((((k >> 3) * 16 + nr) * 8) + (k & 7)) >> 1;
+        if (u == 0) it_u0 |= 1u << r;
+      }
+    }
+    const uint32_t* dense_w = reinterpret_cast<const uint32_t*>(dense);
+    const int dense_plane_w = NT * kOpGroups * p.K / 2;
+    const int b_plane_w = (int)(p.b_bytes / 4);
+    long long it = 0;
+    int ps = 0;            // stage of iteration it
+    uint32_t pphase = 0u;  // parity of (it / stages)
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < p.nUnits && ok; unit += gridDim.x) {
+      const int tp = unit % p.nTP, chunk = unit / p.nTP;
+      const int rt0 = chunk * p.CH, rt1 = min(p.nRT, rt0 + p.CH);
+      // template rows of this template group (zeros past N_B)
+      const int pieces = planes * NT * kOpGroups * p.KC;  // 16-byte pieces
+      for (int base = 0; base < pieces; base += 8 * 32) {
+        uint4 v[8];
+        int dst[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {  // eight loads in flight per lane
+          const int i = base + u * 32 + lane;
+          v[u] = make_uint4(0u, 0u, 0u, 0u);
+          dst[u] = -1;
+          if (i < pieces) {
+            const int kc = i % p.KC;
+            int r = i / p.KC;
+            const int grp = r % kOpGroups;
+            r /= kOpGroups;
+            const int jj = r % NT, pl = r / NT;
+            const int j = tp * NT + jj;
+            dst[u] = ((pl * NT + jj) * kOpGroups + grp) * p.K + kc * 8;
+            if (j < p.N_B) {
+              const uint16_t* src = p.b + pl * p.b_plane +
+                                    ((((long long)(j >> 7) * kOpGroups + grp) * p.KC + kc) * kOpLanes + (j & 127)) * 8;
+              v[u] = __ldg(reinterpret_cast<const uint4*>(src));
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (dst[u] >= 0) *reinterpret_cast<uint4*>(dense + dst[u]) = v[u];
+      }
+      __syncwarp();
+      for (int rt = rt0; rt < rt1 && ok; ++rt) {
+        for (int grp = 0; grp < kOpGroups; ++grp) {
+          const int s = ps;
+          if (p.nprod == 2 && (it & 1) != mine) {
+            ++it;
+            if (++ps == p.stages) {
+              ps = 0;
+              pphase ^= 1u;
+            }
+            continue;
+          }
+          if (it >= p.stages) {
+            int w = 1;
+            if (lane == 0) w = tc_wait(&empty[s], pphase ^ 1u, abort_flag, p.status);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (!w) {
+              ok = false;
+              break;
+            }
+          }
+          unsigned char* st = tc_smem + (size_t)s * p.stage_bytes;
+          if (lane == 0) {
+            mbar_arrive_expect_tx(&full[s], planes * p.a_bytes);
+            const long long off = ((long long)rt * kOpGroups + grp) * p.KC * kOpLanes * 8;
+            for (int pl = 0; pl < planes; ++pl) bulk_g2s(st + pl * p.a_bytes, p.a + pl * p.a_plane + off, p.a_bytes, &full[s]);
+          }
+          // block-diagonal template operand: rows (jj, u, re/im), K-major core matrices
+          uint32_t* bst = reinterpret_cast<uint32_t*>(st + planes * p.a_bytes);
+          const int gofs = grp * p.K / 2;
+#pragma unroll
+          for (int r = 0; r < kMaxItems; ++r) {
+            if (it_src[r] < 0) continue;
+            const bool slot0 = grp == 0 && ((it_u0 >> r) & 1u);
+            for (int pl = 0; pl < planes; ++pl) {
+              const uint32_t v = dense_w[pl * dense_plane_w + gofs + it_src[r]];
+              uint32_t re_row, im_row;
+              if (slot0) {  // slot 0: the real q = 0 and q = Q/2 terms
+                re_row = v & 0x0000FFFFu;
+                im_row = v & 0xFFFF0000u;
+              } else {
+                re_row = v;                                          // (b_re, b_im)
+                im_row = __byte_perm(v, 0u, 0x1032) ^ 0x80000000u;  // (b_im, -b_re)
+              }
+              uint32_t* bp = bst + pl * b_plane_w + it_dst[r];
+              bp[0] = re_row;
+              bp[4] = im_row;  // next row: +8 elements
+            }
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[s]);
+          ++it;
+          if (++ps == p.stages) {
+            ps = 0;
+            pphase ^= 1u;
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) {
+      // copies this warp issued that may still be in flight land before the CTA exits
+      const long long first = it > p.stages ? it - p.stages : 0;
+      for (long long k = first; k < it; ++k)
+        if (p.nprod == 1 || (k & 1) == mine) mbar_wait_bounded(&full[k % p.stages], (uint32_t)((k / p.stages) & 1), kTcBudget);
+    }
+  } else if (warp == 10) {
+    // second producer not used (its template-row copy does not fit)
+  } else if (warp == 1) {
+    // ================= MMA issue (converged warp, one elected lane issues) =================
+    {
+      long long it = 0, tile = 0;
+      int ms = 0;
+      uint32_t mphase = 0u;
+      bool ok = true;
+      constexpr uint32_t kSbo = 128;                 // 8 rows x 16 bytes
+      const uint32_t a_lbo = kOpLanes * 16;          // next 8 components: 128 rows further
+      const uint32_t b_lbo = 16 * 16;                // 16 template rows
+      for (int unit = blockIdx.x; unit < p.nUnits && ok; unit += gridDim.x) {
+        const int chunk = unit / p.nTP;
+        const int rt0 = chunk * p.CH, rt1 = min(p.nRT, rt0 + p.CH);
+        for (int rt = rt0; rt < rt1 && ok; ++rt) {
+          if (tile > 0 && !__all_sync(0xffffffffu, tc_wait(tmem_empty, (uint32_t)((tile - 1) & 1), abort_flag, p.status))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int grp = 0; grp < kOpGroups; ++grp) {
+            const int s = ms;
+            if (!__all_sync(0xffffffffu, tc_wait(&full[s], mphase, abort_flag, p.status))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_addr(tc_smem + (size_t)s * p.stage_bytes);
+            const uint32_t a_hi = st, a_lo = st + p.a_bytes;
+            const uint32_t b_hi = st + planes * p.a_bytes, b_lo = b_hi + p.b_bytes;
+            const uint32_t d = tmem_base + (uint32_t)(grp * 16);
+            for (int ks = 0; ks < p.KS; ++ks) {
+              const uint32_t ao = (uint32_t)ks * 2 * a_lbo, bo = (uint32_t)ks * 2 * b_lbo;
+              tc_mma_f16_elect(d, smem_desc_kmajor(a_hi + ao, a_lbo, kSbo), smem_desc_kmajor(b_hi + bo, b_lbo, kSbo),
+                               p.idesc, ks > 0 ? 1u : 0u);
+              if (p.split) {
+                tc_mma_f16_elect(d, smem_desc_kmajor(a_hi + ao, a_lbo, kSbo), smem_desc_kmajor(b_lo + bo, b_lbo, kSbo),
+                                 p.idesc, 1u);
+                tc_mma_f16_elect(d, smem_desc_kmajor(a_lo + ao, a_lbo, kSbo), smem_desc_kmajor(b_hi + bo, b_lbo, kSbo),
+                                 p.idesc, 1u);
+              }
+            }
+            tc_commit_elect(&empty[s]);
+            ++it;
+            if (++ms == p.stages) {
+              ms = 0;
+              mphase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          tc_commit_elect(tmem_full);
+          ++tile;
+        }
+      }
+      tc_commit_elect(drain);  // every MMA complete before TMEM is released
+      mbar_wait_bounded(drain, 0, kTcBudget);
+      __syncwarp();
+    }
+  } else {
+    // ================= epilogue =================
+    const int qd = warp & 3, sub = (warp - 2) >> 2;
+    const int row = qd * 32 + lane;
+    const int ep = tid - 64;
+    const uint32_t tl = tmem_base + ((uint32_t)(qd * 32) << 16);
+    const int n_local = row / p.T, t = row - n_local * p.T;
+    long long tile = 0;
+    bool run = true;
+    for (int unit = blockIdx.x; unit < p.nUnits && run; unit += gridDim.x) {
+      const int tp = unit % p.nTP, chunk = unit / p.nTP;
+      const int rt0 = chunk * p.CH, rt1 = min(p.nRT, rt0 + p.CH);
+      for (int rt = rt0; rt < rt1; ++rt, ++tile) {
+        const bool got = tc_wait(tmem_full, (uint32_t)(tile & 1), abort_flag, p.status);
+        __syncwarp();
+        tc_fence_after();
+        const long long n = (long long)rt * p.IPT + n_local;
+        const bool row_ok = got && row < p.IPT * p.T && n < p.N_A;
+        float4 r[TPT];
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+          const int jj = sub * TPT + i;
+          const int j = tp * NT + jj;
+          float* xrow = nullptr;
+          if (kWriteX) xrow = p.X + ((n * p.T + t) * (long long)p.N_B + j) * (Q);
+          r[i] = tc_pair<Q, kWriteX>(p, tl, jj, row_ok && j < p.N_B, xrow);
+        }
+        tc_fence_before();
+        mbar_arrive(tmem_empty);
+        if (!kWriteX) {
+          float4* rb = res + (size_t)(tile & 1) * NT * kOpLanes;
+#pragma unroll
+          for (int i = 0; i < TPT; ++i) rb[(sub * TPT + i) * kOpLanes + row] = r[i];
+        }
+        // one decision for all epilogue threads (the flag may change meanwhile)
+        if (named_sync_or(kBarEpi, kEpiThreads, *abort_flag != 0u)) {
+          run = false;
+          break;
+        }
+        for (int e = ep; !kWriteX && e < p.IPT * NT; e += kEpiThreads) {
+          const int nl = e / NT, jj = e % NT;
+          const long long nn = (long long)rt * p.IPT + nl;
+          const int j = tp * NT + jj;
+          if (nn < p.N_A && j < p.N_B) {
+            const float4* rb = res + (size_t)(tile & 1) * NT * kOpLanes + jj * kOpLanes + nl * p.T;
+            float bv = -INFINITY, m = -INFINITY, s = 0.0f;
+            int ba = 0;
+            for (int tt = 0; tt < p.T; ++tt) {
+              const float4 e = rb[tt];
+              if (e.x > bv) {
+                bv = e.x;
+                ba = tt * Q + __float_as_int(e.y);
+              }
+              if (p.lse_on) lse_merge(m, s, e.z, e.w);
+            }
+            const long long o = nn * p.N_B + j;
+            p.best[o] = 6.283185307179586f * bv;
+            p.arg[o] = ba;
+            if (p.lse_on) p.lse[o] = m + logf(s);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+template <int Q>
+int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision, cudaStream_t stream) {
+  using C = TcCfg<Q>;
+  const int planes = operand_planes(precision);
+  p.split = precision == RSVD_BF16X3 ? 1 : 0;
+  p.K = La.K;
+  p.KC = La.KC;
+  p.KS = La.K / 16;
+  p.Hp = La.Hp;
+  p.IPT = La.IPT;
+  p.nRT = (int)La.tiles;
+  p.nTP = (p.N_B + C::NT - 1) / C::NT;
+  p.idesc = idesc_f16(precision == RSVD_FP16 ? 0u : 1u, 128, 16);
+  p.a_bytes = (uint32_t)(kOpLanes * La.K * 2);
+  p.b_bytes = (uint32_t)(16 * La.K * 2);
+  p.stage_bytes = (uint32_t)((planes * (p.a_bytes + p.b_bytes) + 1023) / 1024 * 1024);
+  const uint32_t dense_bytes = (uint32_t)(planes * C::NT * kOpGroups * La.K * 2);  // per producer warp
+  p.dense_bytes = dense_bytes;
+  const uint32_t res_bytes = 2u * C::NT * kOpLanes * 16u;
+  const uint32_t kMaxSmem = 227u * 1024u;
+  // two producer warps (each with its own template-row copy) while three or
+  // more stages still fit, else one
+  p.nprod = (kMaxSmem - (2u * dense_bytes + res_bytes + 1024u)) / p.stage_bytes >= 3 ? 2 : 1;
+  const uint32_t fixed = (uint32_t)p.nprod * dense_bytes + res_bytes + 1024u;
+  int stages = (int)((kMaxSmem - fixed) / p.stage_bytes);
+  if (stages > 6) stages = 6;
+  uint32_t smem = 0;
+  for (; stages >= 2; --stages) {
+    p.stages = stages;
+    p.dense_off = (uint32_t)stages * p.stage_bytes;
+    p.res_off = p.dense_off + (uint32_t)p.nprod * dense_bytes;
+    p.bar_off = p.res_off + res_bytes;
+    smem = p.bar_off + (uint32_t)(2 * stages + 3) * 8u + 8u;
+    if (smem < 120u * 1024u) smem = 120u * 1024u;  // one CTA (and one TMEM allocation) per SM
+    // the allocation also spans the operand descriptors read with their two
+    // byte offsets exchanged (a 16-row-group stride of 2 KB from the last A block)
+    const uint32_t last_a = (uint32_t)(stages - 1) * p.stage_bytes + (uint32_t)(planes - 1) * p.a_bytes;
+    const uint32_t reach = last_a + (uint32_t)(p.KS - 1) * 4096u + 16u * 2048u + 256u;
+    if (smem < reach) smem = reach;
+    if (smem <= kMaxSmem) break;
+  }
+  if (stages < 2) return RSVD_EUNSUPPORTED;
+
+  for (int k = 0; k < Q / 2; ++k) {
+    const double aq = 2.0 * M_PI * k / Q, am = 2.0 * M_PI * k / (Q / 2);
+    p.WQ[k] = make_float2((float)cos(aq), (float)-sin(aq));
+    p.WM[k] = make_float2((float)cos(am), (float)-sin(am));
+  }
+
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RSVD_ECUDA;
+  const long long tiles = (long long)p.nRT * p.nTP;
+  long long ch = tiles / ((long long)sms * 8);
+  if (ch < 1) ch = 1;
+  if (ch > 16) ch = 16;
+  p.CH = (int)ch;
+  const long long units = (long long)((p.nRT + p.CH - 1) / p.CH) * p.nTP;
+  if (units > INT32_MAX) return RSVD_EUNSUPPORTED;
+  p.nUnits = (int)units;
+  const int grid = (int)(units < sms ? units : sms);
+
+  auto kern = write_x ? tc_align_kernel<Q, true> : tc_align_kernel<Q, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RSVD_ECUDA;
+  kern<<<grid, kTcThreads, smem, stream>>>(p);
+  return launch_status();
+}
+
+}  // namespace
+
+// Shared entry of rsvd_align_best / rsvd_align_scores for the operand forms.
+RSVD_HIDDEN int align_tc(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
+                         float inv_sigma2, float* best, int32_t* arg, float* lse, float* X, cudaStream_t stream) {
+  OperandLayout La{}, Lb{};
+  if (!is_operand_precision(precision)) return RSVD_EUNSUPPORTED;
+  if (!make_operand_layout(N_A, T, H, Q, &La) || !make_operand_layout(N_B, 1, H, Q, &Lb)) return RSVD_EUNSUPPORTED;
+  TcParams p{};
+  p.a = static_cast<const uint16_t*>(cA);
+  p.b = static_cast<const uint16_t*>(cB);
+  p.a_plane = La.plane_elems;
+  p.b_plane = Lb.plane_elems;
+  p.best = best;
+  p.arg = arg;
+  p.lse = lse;
+  p.X = X;
+  p.status = status_word();
+  p.N_A = N_A;
+  p.T = T;
+  p.N_B = N_B;
+  p.lse_on = lse ? 1 : 0;
+  p.inv_sigma2 = inv_sigma2;
+  if (Q == 128) return launch_tc<128>(p, X != nullptr, La, precision, stream);
+  return launch_tc<256>(p, X != nullptr, La, precision, stream);
+}
+
+}  // namespace rsvd

@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include "compress_v2.cuh"
+#include "operand.cuh"
 
 namespace rsvd {
 namespace {
@@ -154,7 +155,13 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
     return RSVD_EINVAL;
   }
   if (T > kMaxT) return RSVD_EUNSUPPORTED;
-  if (precision != RSVD_FP32) return RSVD_EUNSUPPORTED;
+  OperandLayout OL{};
+  const bool fits_v2 = R * (Q / 2) * 8 <= 96 * 1024;
+  if (precision != RSVD_FP32) {
+    // operand forms are written by the shared-memory kernel only
+    if (!is_operand_precision(precision) || !fits_v2) return RSVD_EUNSUPPORTED;
+    if (!make_operand_layout(N, T, H, Q, &OL)) return RSVD_EUNSUPPORTED;
+  }
   if (((uintptr_t)polar & 7u) || ((uintptr_t)out & 15u) || ((uintptr_t)U & 7u)) return RSVD_EINVAL;
   if ((size_t)N * T > (size_t)INT32_MAX / 2) return RSVD_EUNSUPPORTED;
 
@@ -195,6 +202,14 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
     bool uniform = k[0] > 0.0;
     for (int r = 0; r < R && uniform; ++r) uniform = fabs(k[r] - (r + 1) * k[0]) <= 1e-9 * k[R - 1];
     q.uniform = uniform ? 1 : 0;
+    q.precision = precision;
+    q.planes = static_cast<uint16_t*>(out);
+    q.L = OL;
+    if (precision != RSVD_FP32) {
+      // padding components, lanes and tiles of the operand planes are zero
+      const size_t bytes = (size_t)operand_planes(precision) * (size_t)OL.plane_elems * 2;
+      if (cudaMemsetAsync(out, 0, bytes, static_cast<cudaStream_t>(stream)) != cudaSuccess) return RSVD_ECUDA;
+    }
     q.dk = (float)k[0];
     for (int r = 0; r < R; ++r) {
       q.k[r] = p.k[r];
@@ -204,9 +219,8 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
       q.dx[t] = p.dx[t];
       q.dy[t] = p.dy[t];
     }
-    const int rc2 = (R * (Q / 2) * 8 <= 96 * 1024) ? launch_compress_v2(q, static_cast<cudaStream_t>(stream))
-                                                     : RSVD_EUNSUPPORTED;
-    if (rc2 != RSVD_EUNSUPPORTED) return rc2;
+    const int rc2 = fits_v2 ? launch_compress_v2(q, static_cast<cudaStream_t>(stream)) : RSVD_EUNSUPPORTED;
+    if (rc2 != RSVD_EUNSUPPORTED || precision != RSVD_FP32) return rc2;
   }
   const int M = Q / 2;
   const int L = M < kThreads ? M : kThreads;

@@ -152,7 +152,23 @@ __global__ void __launch_bounds__(kNT) compress2_kernel(const __grid_constant__ 
           for (int k1 = 0; k1 < P1; ++k1) x[k1 * XP + tp] = z[k1];
         }
         __syncwarp();
-        if (valid && t < T && h < H) {
+        if (valid && t < T && h < H && p.precision != RSVD_FP32) {
+#pragma unroll
+          for (int i = 0; i < RR; ++i) {
+            const int k1 = tp * RR + i;
+            float2 y[P2];
+#pragma unroll
+            for (int q2 = 0; q2 < P2; ++q2) y[q2] = x[k1 * XP + q2];
+            RegDft<P2>::run(y);
+#pragma unroll
+            for (int k2 = 0; k2 < P2 / 2; ++k2) {
+              const int q = k1 + P1 * k2;
+              const float2 v = (q == 0) ? make_float2(y[0].x * invQ, y[P2 / 2].x * invQ)
+                                        : make_float2(y[k2].x * invQ, y[k2].y * invQ);
+              operand_put(p.planes, p.L.plane_elems, p.precision, operand_index(p.L, n, t, h, q), v);
+            }
+          }
+        } else if (valid && t < T && h < H) {
           float2* o = p.out + (((size_t)n * T + t) * H + h) * M;
 #pragma unroll
           for (int i = 0; i < RR; ++i) {

@@ -3,7 +3,7 @@
 
 #include <type_traits>
 
-#include "rsvd_internal.cuh"
+#include "operand.cuh"
 
 namespace rsvd {
 
@@ -18,6 +18,11 @@ struct Compress2Params {
   float sw[kMaxR];
   float dx[kMaxT];
   float dy[kMaxT];
+  // RSVD_FP32: write `out`; otherwise round into the operand planes `planes`
+  // (layout `L`, operand.cuh)
+  int precision;
+  uint16_t* planes;
+  OperandLayout L;
 };
 
 // RSVD_EUNSUPPORTED when Q or the shared-memory footprint is outside its range.

@@ -67,4 +67,20 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(count) : "memory");
 }
 
+// Named barrier that also returns the OR of `pred` over the participating threads.
+__device__ __forceinline__ int named_sync_or(int id, int count, int pred) {
+  int r;
+  asm volatile(
+      "{\n"
+      ".reg .pred p, q;\n"
+      "setp.ne.b32 p, %3, 0;\n"
+      "bar.red.or.pred q, %1, %2, p;\n"
+      "selp.b32 %0, 1, 0, q;\n"
+      "}\n"
+      : "=r"(r)
+      : "r"(id), "r"(count), "r"(pred)
+      : "memory");
+  return r;
+}
+
 }  // namespace rsvd

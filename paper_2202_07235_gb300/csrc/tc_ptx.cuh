@@ -1,0 +1,210 @@
+// Inline-PTX wrappers for the 5th-generation tensor cores (tcgen05): tensor
+// memory (TMEM) allocation, loads and stores, the single-thread MMA issue and
+// its completion tracking through an mbarrier, and the shared-memory matrix
+// descriptors of the canonical (no-swizzle) K-major operand layout.
+#pragma once
+
+#include <stdint.h>
+
+#include "ptx_sync.cuh"
+
+namespace rsvd {
+
+// ---- TMEM allocation (one full warp executes each of these) ----
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// ---- ordering of tcgen05 operations around thread synchronisation ----
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Generic-proxy shared-memory writes made visible to the async proxy (the
+// tensor core reads its operands through it).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (bf16 or fp16 operands, FP32
+// accumulate). Issued by one thread; asynchronous.
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// The same, issued by one elected lane of a converged warp (the operands stay
+// warp-uniform, which keeps the issue rate high).
+__device__ __forceinline__ void tc_mma_f16_elect(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p, e;\n"
+      "elect.sync _|e, 0xffffffff;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit_elect(uint64_t* bar) {
+  asm volatile(
+      "{\n"
+      ".reg .pred e;\n"
+      "elect.sync _|e, 0xffffffff;\n"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+      "}\n" ::"r"(smem_addr(bar))
+      : "memory");
+}
+
+// Arrive (once) on `bar` when every MMA this thread issued so far has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes stored as 128 contiguous bytes;
+// `lbo` = byte distance between core matrices adjacent along K,
+// `sbo` = byte distance between core matrices adjacent along M (or N).
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor core
+  // base offset 0, relative LBO, swizzle mode 0 (none)
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, both operands K-major.
+// ab_format: 0 = fp16, 1 = bf16.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_format, int M, int N) {
+  return (1u << 4)                        // D format: f32
+         | (ab_format << 7)               // A format
+         | (ab_format << 10)              // B format
+         | ((uint32_t)(N >> 3) << 17)     // N / 8
+         | ((uint32_t)(M >> 4) << 24);    // M / 16
+}
+
+// ---- TMEM -> registers. Warp w reads lanes 32*(w%4) .. +31 (taddr carries
+// that lane base); thread i gets its lane's `n` consecutive columns. Each
+// wrapper waits for its loads before returning, so the registers are valid.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float2& v) {
+  uint32_t a, b;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(a), "=r"(b)
+      : "r"(taddr)
+      : "memory");
+  v = make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+
+// Eight loads of 2 columns at taddr + i * stride (i = 0..7), one wait.
+__device__ __forceinline__ void tmem_ld2x8(uint32_t taddr, uint32_t stride, float2 (&v)[8]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%17];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%18];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%19];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%20];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%21];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%22];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14, %15}, [%23];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr), "r"(taddr + stride), "r"(taddr + 2 * stride), "r"(taddr + 3 * stride),
+        "r"(taddr + 4 * stride), "r"(taddr + 5 * stride), "r"(taddr + 6 * stride), "r"(taddr + 7 * stride)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+}
+
+// `N` complex values (2N columns) from one column block, and the same from a
+// second block, one wait (N = 2 or 4).
+template <int N>
+__device__ __forceinline__ void tmem_ld_pair(uint32_t ta, uint32_t tb, float2 (&a)[N], float2 (&b)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld_pair<2>(uint32_t ta, uint32_t tb, float2 (&a)[2], float2 (&b)[2]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%8];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%9];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[4 + 2 * i]), __uint_as_float(r[4 + 2 * i + 1]));
+  }
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld_pair<4>(uint32_t ta, uint32_t tb, float2 (&a)[4], float2 (&b)[4]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[8 + 2 * i]), __uint_as_float(r[8 + 2 * i + 1]));
+  }
+}
+
+// Registers -> TMEM: `N` complex values (2N columns) at taddr. The caller
+// issues tmem_wait_st() before the columns are read back.
+template <int N>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float2 (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_st<2>(uint32_t taddr, const float2 (&v)[2]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr),
+               "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[1].x)),
+               "r"(__float_as_uint(v[1].y))
+               : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_st<4>(uint32_t taddr, const float2 (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+               "r"(__float_as_uint(v[0].x)), "r"(__float_as_uint(v[0].y)), "r"(__float_as_uint(v[1].x)),
+               "r"(__float_as_uint(v[1].y)), "r"(__float_as_uint(v[2].x)), "r"(__float_as_uint(v[2].y)),
+               "r"(__float_as_uint(v[3].x)), "r"(__float_as_uint(v[3].y))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+}  // namespace rsvd

@@ -63,7 +63,14 @@ def test_size_queries(lib):
     lib.rsvd_compressed_bytes.restype = ctypes.c_size_t
     lib.rsvd_compressed_bytes.argtypes = [ctypes.c_int] * 5
     assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 0) == 8192 * 9 * 12 * 128 * 8
-    assert lib.rsvd_compressed_bytes(8, 1, 12, 256, 2) == 0  # precision not implemented
+    # operand forms: planes x tiles x 32 groups x K x 128 lanes x 2 bytes, K = 2 Hp (Q/64)
+    assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 1) == 586 * 32 * 96 * 128 * 2      # 14 images / tile
+    assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 3) == 2 * 586 * 32 * 96 * 128 * 2
+    assert lib.rsvd_compressed_bytes(256, 1, 6, 128, 2) == 2 * 32 * 32 * 128 * 2           # H 6 -> 8
+    assert lib.rsvd_compressed_bytes(8, 1, 5, 256, 1) == 1 * 32 * 48 * 128 * 2             # H 5 -> 6
+    assert lib.rsvd_compressed_bytes(8, 1, 12, 512, 2) == 0  # tensor-core forms: Q in {128, 256}
+    assert lib.rsvd_compressed_bytes(8, 1, 33, 256, 3) == 0
+    assert lib.rsvd_compressed_bytes(8, 1, 12, 256, 7) == 0
     lib.rsvd_build_workspace_bytes.restype = ctypes.c_size_t
     lib.rsvd_build_workspace_bytes.argtypes = [ctypes.c_int] * 3
     assert lib.rsvd_build_workspace_bytes(64, 256, 1024) >= 3 * 64 * 64 * 8
@@ -78,9 +85,11 @@ def test_argument_errors_return_codes_without_a_gpu(lib):
     one = ctypes.c_void_p(16)
     # NULL operands
     assert f(None, 1, 1, one, 1, 8, 256, 0, 1.0, one, one, None, None) == -1
-    # Q not a power of two / precision not implemented / H too large
+    # Q not a power of two / unknown precision / tensor-core form outside its Q and H range / H too large
     assert f(one, 1, 1, one, 1, 8, 100, 0, 1.0, one, one, None, None) == -2
-    assert f(one, 1, 1, one, 1, 8, 256, 3, 1.0, one, one, None, None) == -2
+    assert f(one, 1, 1, one, 1, 8, 256, 5, 1.0, one, one, None, None) == -2
+    assert f(one, 1, 1, one, 1, 8, 512, 3, 1.0, one, one, None, None) == -2
+    assert f(one, 1, 1, one, 1, 33, 256, 1, 1.0, one, one, None, None) == -2
     assert f(one, 1, 1, one, 1, 65, 256, 0, 1.0, one, one, None, None) == -2
     # log-sum-exp requested with a non-positive scale
     assert f(one, 1, 1, one, 1, 8, 256, 0, 0.0, one, one, one, None) == -1

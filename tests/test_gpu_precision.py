@@ -1,0 +1,228 @@
+"""Tensor-core operand forms (bf16, fp16, split-bf16x3) through the C ABI.
+
+* pack: bit-exact against the header's layout filled with the oracle's
+  round-to-nearest of the same FP32 coefficients;
+* compress with an operand precision: byte-identical to pack of the FP32
+  compression;
+* align_scores / align_best: against the oracle's score of the same form on
+  the same FP32 coefficients (only FP32 accumulation and the FP32 transform
+  differ: RTOL of the FP32 path), over ragged tiles and template groups;
+* end to end (polar samples in): split-bf16x3 within 1e-5 of the FP64 oracle
+  on X, argmax identical on noiseless inputs; single-pass errors reported.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from tests.gpu_common import RTOL, check_best, pack_slots, setup  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2202_07235_gb300 as P  # noqa: E402
+
+DEV = "cuda:0"
+FORMS = ("bf16", "fp16", "bf16x3")
+
+
+def _layout(N, T, H, Q):
+    g = Q // 64
+    step = 8 // g
+    Hp = -(-H // step) * step
+    K = 2 * Hp * g
+    IPT = 128 // T
+    tiles = -(-N // IPT)
+    return g, Hp, K, IPT, tiles
+
+
+def expected_planes(c32_slots, N, T, H, Q, form):
+    """Operand planes (uint16) from FP32 packed slots [N*T, H, Q/2, 2], following
+    the layout stated in include/rsvd.h, values rounded by the oracle."""
+    g, Hp, K, IPT, tiles = _layout(N, T, H, Q)
+    x = c32_slots.astype(np.float64).reshape(N, T, H, Q // 2, 2)
+    rn = O.round_bf16 if form in ("bf16", "bf16x3") else O.round_fp16
+    hi = rn(x)
+    parts = [hi] if form != "bf16x3" else [hi, O.round_bf16(x - hi)]
+    out = []
+    for v in parts:
+        if form == "fp16":
+            bits = v.astype(np.float16).view(np.uint16)
+        else:
+            bits = (v.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+        plane = np.zeros((tiles, 32, K // 8, 128, 8), dtype=np.uint16)
+        n, t, h, s, c = np.meshgrid(np.arange(N), np.arange(T), np.arange(H), np.arange(Q // 2), np.arange(2),
+                                    indexing="ij")
+        k = (s // 32) * 2 * Hp + 2 * h + c
+        plane[n // IPT, s % 32, k // 8, (n % IPT) * T + t, k % 8] = bits
+        out.append(plane.reshape(-1))
+    return np.concatenate(out)
+
+
+def _oracle_c32(wl, A, B, U):
+    """Oracle compressed rings cast to FP32: (a32 full spectrum, b32, packed slots)."""
+    g = wl.grid
+    a = O.compress(O.translate(A.astype(np.complex128), g.k, wl.deltas), U, g.w)
+    b = O.compress(B.astype(np.complex128), U, g.w)
+    a32 = a.astype(np.complex64).astype(np.complex128)
+    b32 = b.astype(np.complex64).astype(np.complex128)
+    return a32, b32, pack_slots(a32).astype(np.float32), pack_slots(b32).astype(np.float32)
+
+
+CASES = [  # Q, R, H, T_side, N_A, N_B
+    (128, 32, 8, 1, 19, 7),
+    (128, 32, 6, 1, 130, 9),     # H padded to 8; two image tiles; 3 template groups (ragged)
+    (256, 64, 12, 3, 30, 5),     # 14 images per tile, ragged last tile and template pair
+    (256, 64, 5, 2, 33, 4),      # H padded to 6
+]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("Q,R,H,T_side,N_A,N_B", CASES[:2] + CASES[2:3])
+def test_pack_is_bit_exact(form, Q, R, H, T_side, N_A, N_B):
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, seed=Q + H)
+    T = wl.deltas.shape[0]
+    _, _, sa, _ = _oracle_c32(wl, A, B, U)
+    got = P.pack(torch.from_numpy(sa).to(DEV), N_A, T, H, Q, form)
+    P.status()
+    exp = expected_planes(sa, N_A, T, H, Q, form)
+    assert got.numel() == exp.size * 2
+    assert np.array_equal(got.cpu().numpy().view(np.uint16), exp)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_compress_operand_form_equals_pack_of_fp32(form):
+    wl, A, B, U = setup(N=128, R=64, Q=256, N_B=3, N_A=17, T_side=3, H=12, seed=5)
+    g = wl.grid
+    At, Ut = torch.from_numpy(A).to(DEV), torch.from_numpy(U).to(DEV)
+    c32 = P.compress(g.k, g.w, Ut, At, deltas=wl.deltas)
+    c16 = P.compress(g.k, g.w, Ut, At, deltas=wl.deltas, precision=form)
+    ref = P.pack(c32, 17, 9, 12, 256, form)
+    P.status()
+    assert torch.equal(c16, ref)
+
+
+def _gpu_form(sa, sb, N_A, T, N_B, H, Q, form):
+    cA = P.pack(torch.from_numpy(sa).to(DEV), N_A, T, H, Q, form)
+    cB = P.pack(torch.from_numpy(sb).to(DEV), N_B, 1, H, Q, form)
+    return cA, cB
+
+
+def _pair_scale_err(Xg, Xr):
+    nA, T, nB, Q = Xr.shape
+    scale = np.max(np.abs(np.transpose(Xr, (0, 2, 1, 3)).reshape(nA, nB, -1)), axis=-1)
+    err = np.abs(Xg - Xr) / scale[:, None, :, None]
+    return float(err.max())
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("Q,R,H,T_side,N_A,N_B", CASES)
+def test_align_scores_match_oracle_form(form, Q, R, H, T_side, N_A, N_B):
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, seed=3 * Q + H)
+    T = wl.deltas.shape[0]
+    a32, b32, sa, sb = _oracle_c32(wl, A, B, U)
+    cA, cB = _gpu_form(sa, sb, N_A, T, N_B, H, Q, form)
+    X = P.align_scores(cA, N_A, T, cB, N_B, H, Q, precision=form)
+    P.status()
+    Xr = O.scores_compressed_form(a32, b32, form)
+    assert _pair_scale_err(X.cpu().numpy().astype(np.float64), Xr) <= RTOL
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("Q,R,H,T_side,N_A,N_B", CASES)
+def test_align_best_match_oracle_form(form, Q, R, H, T_side, N_A, N_B):
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, seed=5 * Q + H)
+    T = wl.deltas.shape[0]
+    a32, b32, sa, sb = _oracle_c32(wl, A, B, U)
+    cA, cB = _gpu_form(sa, sb, N_A, T, N_B, H, Q, form)
+    best, arg, lse = P.align_best(cA, N_A, T, cB, N_B, H, Q, inv_sigma2=0.7, want_lse=True, precision=form)
+    P.status()
+    Xr = O.scores_compressed_form(a32, b32, form)
+    check_best(Xr, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 0.7)
+
+
+def _end_to_end(form, Q, R, H, T_side, N_A, N_B, snr=0.1, seed=0):
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, snr=snr, seed=seed)
+    g = wl.grid
+    T = wl.deltas.shape[0]
+    Ut = torch.from_numpy(U).to(DEV)
+    cA = P.compress(g.k, g.w, Ut, torch.from_numpy(A).to(DEV), deltas=wl.deltas if T > 1 else None, precision=form)
+    cB = P.compress(g.k, g.w, Ut, torch.from_numpy(B).to(DEV), precision=form)
+    a = O.compress(O.translate(A.astype(np.complex128), g.k, wl.deltas), U, g.w)
+    b = O.compress(B.astype(np.complex128), U, g.w)
+    Xr = O.scores_compressed(a, b).real
+    return wl, cA, cB, T, Xr
+
+
+@pytest.mark.parametrize("H", [8, 12, 16, 24])
+def test_split_bf16x3_within_1e5_of_fp64_oracle(H):
+    """The precision-study geometry (64 px, 32 rings, Q = 128) end to end."""
+    wl, cA, cB, T, Xr = _end_to_end("bf16x3", 128, 32, H, 1, 64, 16, seed=H)
+    X = P.align_scores(cA, 64, T, cB, 16, H, 128, precision="bf16x3").cpu().numpy().astype(np.float64)
+    P.status()
+    rel_f = np.linalg.norm(X - Xr) / np.linalg.norm(Xr)
+    assert rel_f <= 1e-5, rel_f
+    assert _pair_scale_err(X, Xr) <= 1e-5
+
+
+def test_split_bf16x3_throughput_geometry_within_1e5():
+    wl, cA, cB, T, Xr = _end_to_end("bf16x3", 256, 64, 12, 3, 20, 6, snr=0.05, seed=9)
+    best, arg, lse = P.align_best(cA, 20, T, cB, 6, 12, 256, want_lse=True, precision="bf16x3")
+    X = P.align_scores(cA, 20, T, cB, 6, 12, 256, precision="bf16x3").cpu().numpy().astype(np.float64)
+    P.status()
+    assert np.linalg.norm(X - Xr) / np.linalg.norm(Xr) <= 1e-5
+    check_best(Xr, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
+
+
+def test_split_bf16x3_noiseless_argmax_identical():
+    """Full rank (H = R = 32) on noiseless images made as T_{-delta_t0} R_{gamma_m0} B_j0."""
+    from synthetic import make_workload
+
+    Q = 128
+    wl = make_workload(N=64, R=32, Q=Q, N_B=6, N_A=10, snr=None, T_side=3, seed=11)
+    A = wl.images.astype(np.complex64)
+    B = wl.templates.astype(np.complex64)
+    H = 32
+    U, _ = O.principal_vectors(O.radial_kernel(B.astype(np.complex128), wl.grid.w), H)
+    g = wl.grid
+    Ut = torch.from_numpy(U).to(DEV)
+    cA = P.compress(g.k, g.w, Ut, torch.from_numpy(A).to(DEV), deltas=wl.deltas, precision="bf16x3")
+    cB = P.compress(g.k, g.w, Ut, torch.from_numpy(B).to(DEV), precision="bf16x3")
+    best, arg, _ = P.align_best(cA, 10, 9, cB, 6, H, Q, precision="bf16x3")
+    P.status()
+    a = O.compress(O.translate(A.astype(np.complex128), g.k, wl.deltas), U, g.w)
+    b = O.compress(B.astype(np.complex128), U, g.w)
+    Xr = O.scores_compressed(a, b).real
+    mask = np.zeros((10, 6), dtype=bool)
+    mask[np.arange(10), wl.truth_j] = True
+    check_best(Xr, best.cpu().numpy(), arg.cpu().numpy(), exact_arg_mask=mask)
+    arg = arg.cpu().numpy()
+    for n in range(10):
+        assert arg[n, wl.truth_j[n]] == wl.truth_t[n] * Q + wl.truth_m[n]
+
+
+@pytest.mark.parametrize("form,bound", [("bf16", 5e-3), ("fp16", 1e-3)])
+def test_single_pass_error_is_bounded(form, bound):
+    """Single-pass forms: relative Frobenius error on X against the FP64 oracle
+    stays within the rounding of 8 (bf16) or 11 (fp16) significand bits."""
+    wl, cA, cB, T, Xr = _end_to_end(form, 128, 32, 12, 1, 64, 16, seed=4)
+    X = P.align_scores(cA, 64, T, cB, 16, 12, 128, precision=form).cpu().numpy().astype(np.float64)
+    P.status()
+    rel_f = np.linalg.norm(X - Xr) / np.linalg.norm(Xr)
+    print(f"{form}: relative Frobenius error on X {rel_f:.3e}")
+    assert rel_f <= bound
+
+
+def test_operand_forms_reject_unsupported_sizes():
+    x = torch.zeros(16, device=DEV)
+    with pytest.raises(P.RSVDError):
+        P.align_best(x, 1, 1, x, 1, 8, 512, precision="bf16")
+    with pytest.raises(P.RSVDError):
+        P.align_best(x, 1, 1, x, 1, 33, 256, precision="bf16x3")
+    with pytest.raises(P.RSVDError):  # split operands at Q = 256: shared memory holds H <= 18
+        P.align_best(x, 1, 1, x, 1, 20, 256, precision="bf16x3")
+    assert P.compressed_bytes(4, 1, 8, 64, "bf16") == 0
