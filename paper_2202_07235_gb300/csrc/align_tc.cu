@@ -73,26 +73,69 @@ struct TcParams {
   int* status;
   int N_A, T, N_B, IPT, nRT, nTP, CH, nUnits;
   int K, KC, KS, Hp, stages, split, lse_on, nprod;
+  int bres;  // template blocks of all 32 groups resident for a whole work unit (single-pass forms)
   float inv_sigma2;
   uint32_t idesc;
-  uint32_t stage_bytes, a_bytes, b_bytes, dense_off, dense_bytes, res_off, bar_off;
+  uint32_t stage_bytes, a_bytes, b_bytes, dense_off, dense_bytes, bres_off, res_off, bar_off;
   float2 WQ[128];  // W_Q^k = exp(-2 pi i k / Q), k < Q/2
   float2 WM[128];  // W_M^k, M = Q/2
 };
 
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                        int* status) {
+// Bounded wait for a barrier phase. The abort flag and the clock are checked
+// every 16 polls; `sleep_ns` > 0 backs off between polls (long waits of many
+// threads, which would otherwise keep the shared-memory pipe busy).
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag, int* status,
+                                        unsigned sleep_ns = 0) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kTcBudget) {
-      record(status, kDevTimeout);
-      *abort_flag = 1;
-      return false;
+  for (unsigned n = 1;; ++n) {
+    if (sleep_ns) __nanosleep(sleep_ns);
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 15u) == 0u) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kTcBudget) {
+        record(status, kDevTimeout);
+        *abort_flag = 1;
+        return false;
+      }
     }
   }
-  return true;
+}
+
+// The MMA chain of one group: K-steps ks = 0..KS-1 (descriptor start addresses
+// advance by a_step / b_step), bf16x3 adding the A_hi B_lo and A_lo B_hi terms.
+template <int KS, bool kSplit>
+__device__ __forceinline__ void issue_group(uint32_t leader, uint32_t d, uint64_t ad, uint64_t bd, uint64_t ad_lo,
+                                            uint64_t bd_lo, uint64_t a_step, uint64_t b_step, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    tc_mma_f16_by(leader, d, ad + ks * a_step, bd + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+    if (kSplit) {
+      tc_mma_f16_by(leader, d, ad + ks * a_step, bd_lo + ks * b_step, idesc, 1u);
+      tc_mma_f16_by(leader, d, ad_lo + ks * a_step, bd + ks * b_step, idesc, 1u);
+    }
+  }
+}
+
+template <bool kSplit>
+__device__ __forceinline__ void issue_group_rt(int KS, uint32_t leader, uint32_t d, uint64_t ad, uint64_t bd,
+                                               uint64_t ad_lo, uint64_t bd_lo, uint64_t a_step, uint64_t b_step,
+                                               uint32_t idesc) {
+  switch (KS) {
+    case 2: issue_group<2, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
+    case 3: issue_group<3, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
+    case 4: issue_group<4, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
+    case 6: issue_group<6, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
+    case 8: issue_group<8, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
+    default:
+      for (int ks = 0; ks < KS; ++ks) {
+        tc_mma_f16_by(leader, d, ad + ks * a_step, bd + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+        if (kSplit) {
+          tc_mma_f16_by(leader, d, ad + ks * a_step, bd_lo + ks * b_step, idesc, 1u);
+          tc_mma_f16_by(leader, d, ad_lo + ks * a_step, bd + ks * b_step, idesc, 1u);
+        }
+      }
+  }
 }
 
 // Z(k) = [X + conj P] + i w [X - conj P]
@@ -113,11 +156,20 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
   const uint32_t cb = (uint32_t)(jj * 2 * g);
 
   // ---- first stage: pre-processing, g-point DFTs, twiddles; in place ----
+  // (the loads of the next group pair are in flight while this one is computed)
+  uint32_t cur[4 * g], nxt[4 * g];
+  tmem_ld_pair_issue<g>(tl + cb, tl + cb, cur);
+  tmem_wait_ld_tie<4 * g>(cur);
 #pragma unroll
   for (int k1 = 0; k1 <= 16; ++k1) {
     const int k2 = (32 - k1) & 31;
+    if (k1 < 16) tmem_ld_pair_issue<g>(tl + (k1 + 1) * 16 + cb, tl + ((31 - k1) & 31) * 16 + cb, nxt);
     float2 xa[g], xb[g], za[g], zb[g];
-    tmem_ld_pair<g>(tl + k1 * 16 + cb, tl + k2 * 16 + cb, xa, xb);
+#pragma unroll
+    for (int i = 0; i < g; ++i) {
+      xa[i] = make_float2(__uint_as_float(cur[2 * i]), __uint_as_float(cur[2 * i + 1]));
+      xb[i] = make_float2(__uint_as_float(cur[2 * g + 2 * i]), __uint_as_float(cur[2 * g + 2 * i + 1]));
+    }
     if (k1 == 0) {
       za[0] = make_float2(xa[0].x + xa[0].y, xa[0].x - xa[0].y);  // X_hat(0), X_hat(M) real
 #pragma unroll
@@ -146,6 +198,11 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
       for (int p1 = 1; p1 < g; ++p1) zb[p1] = cmul(zb[p1], p.WM[k2 * p1]);
       tmem_st<g>(tl + k2 * 16 + cb, zb);
     }
+    if (k1 < 16) {
+      tmem_wait_ld_tie<4 * g>(nxt);
+#pragma unroll
+      for (int i = 0; i < 4 * g; ++i) cur[i] = nxt[i];
+    }
   }
   tmem_wait_st();
 
@@ -157,12 +214,16 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
 #pragma unroll
   for (int p1 = 0; p1 < g; ++p1) {
     float2 z[32];
+    {
+      uint32_t r[4][16];  // all 32 loads of the pass in flight, then one wait
 #pragma unroll
-    for (int b8 = 0; b8 < 4; ++b8) {
-      float2 w8[8];
-      tmem_ld2x8(tl + (uint32_t)(b8 * 8 * 16) + cb + 2 * p1, 16, w8);
+      for (int b8 = 0; b8 < 4; ++b8) tmem_ld2x8_issue(tl + (uint32_t)(b8 * 8 * 16) + cb + 2 * p1, 16, r[b8]);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) z[b8 * 8 + i] = w8[i];
+      for (int b8 = 0; b8 < 4; ++b8) tmem_wait_ld_tie<16>(r[b8]);
+#pragma unroll
+      for (int b8 = 0; b8 < 4; ++b8)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[b8 * 8 + i] = make_float2(__uint_as_float(r[b8][2 * i]), __uint_as_float(r[b8][2 * i + 1]));
     }
     RegDft<32>::run(z);  // z[p2] = X(2p) + i X(2p+1) over 2 pi, p = p1 + g p2
     if (kWriteX) {
@@ -229,9 +290,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
     fence_mbar_init();
   }
   // the template blocks' zeros never change: clear them once
-  for (int s = 0; s < p.stages; ++s) {
-    uint32_t* bz = reinterpret_cast<uint32_t*>(tc_smem + (size_t)s * p.stage_bytes + planes * p.a_bytes);
-    for (int i = tid; i < (int)(planes * p.b_bytes / 4); i += kTcThreads) bz[i] = 0u;
+  if (p.bres) {
+    uint32_t* bz = reinterpret_cast<uint32_t*>(tc_smem + p.bres_off);
+    for (int i = tid; i < (int)(kOpGroups * p.b_bytes / 4); i += kTcThreads) bz[i] = 0u;
+  } else {
+    for (int s = 0; s < p.stages; ++s) {
+      uint32_t* bz = reinterpret_cast<uint32_t*>(tc_smem + (size_t)s * p.stage_bytes + planes * p.a_bytes);
+      for (int i = tid; i < (int)(planes * p.b_bytes / 4); i += kTcThreads) bz[i] = 0u;
+    }
   }
   fence_proxy_async_smem();
   if (warp == 1) {
@@ -272,7 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
     const uint32_t* dense_w = reinterpret_cast<const uint32_t*>(dense);
     const int dense_plane_w = NT * kOpGroups * p.K / 2;
     const int b_plane_w = (int)(p.b_bytes / 4);
-    long long it = 0;
+    long long it = 0, ptile = 0;
     int ps = 0;            // stage of iteration it
     uint32_t pphase = 0u;  // parity of (it / stages)
     bool ok = true;
@@ -309,7 +375,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           if (dst[u] >= 0) *reinterpret_cast<uint4*>(dense + dst[u]) = v[u];
       }
       __syncwarp();
-      for (int rt = rt0; rt < rt1 && ok; ++rt) {
+      if (p.bres) {
+        // resident template blocks of this warp's groups: rewritten only after every
+        // MMA of the previous unit (the last tile committed to tmem_full) is done
+        if (ptile > 0) {
+          int w = 1;
+          if (lane == 0) w = tc_wait(tmem_full, (uint32_t)((ptile - 1) & 1), abort_flag, p.status);
+          if (!__shfl_sync(0xffffffffu, w, 0)) {
+            ok = false;
+            break;
+          }
+        }
+        for (int grp = (int)mine; grp < kOpGroups; grp += p.nprod) {
+          uint32_t* bp0 = reinterpret_cast<uint32_t*>(tc_smem + p.bres_off + (size_t)grp * p.b_bytes);
+          const int gofs = grp * p.K / 2;
+#pragma unroll
+          for (int r = 0; r < kMaxItems; ++r) {
+            if (it_src[r] < 0) continue;
+            const uint32_t v = dense_w[gofs + it_src[r]];
+            const bool slot0 = grp == 0 && ((it_u0 >> r) & 1u);
+            bp0[it_dst[r]] = slot0 ? (v & 0x0000FFFFu) : v;
+            bp0[it_dst[r] + 4] = slot0 ? (v & 0xFFFF0000u) : (__byte_perm(v, 0u, 0x1032) ^ 0x80000000u);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+      }
+      for (int rt = rt0; rt < rt1 && ok; ++rt, ++ptile) {
         for (int grp = 0; grp < kOpGroups; ++grp) {
           const int s = ps;
           if (p.nprod == 2 && (it & 1) != mine) {
@@ -339,7 +431,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           uint32_t* bst = reinterpret_cast<uint32_t*>(st + planes * p.a_bytes);
           const int gofs = grp * p.K / 2;
 #pragma unroll
-          for (int r = 0; r < kMaxItems; ++r) {
+          for (int r = 0; r < (p.bres ? 0 : kMaxItems); ++r) {
             if (it_src[r] < 0) continue;
             const bool slot0 = grp == 0 && ((it_u0 >> r) & 1u);
             for (int pl = 0; pl < planes; ++pl) {
@@ -379,6 +471,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
   } else if (warp == 1) {
     // ================= MMA issue (converged warp, one elected lane issues) =================
     {
+      const uint32_t mma_leader = elect_one();  // the same lane issues every MMA and commit
       long long it = 0, tile = 0;
       int ms = 0;
       uint32_t mphase = 0u;
@@ -404,20 +497,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
             tc_fence_after();
             const uint32_t st = smem_addr(tc_smem + (size_t)s * p.stage_bytes);
             const uint32_t a_hi = st, a_lo = st + p.a_bytes;
-            const uint32_t b_hi = st + planes * p.a_bytes, b_lo = b_hi + p.b_bytes;
+            const uint32_t b_hi = p.bres ? smem_addr(tc_smem + p.bres_off + (size_t)grp * p.b_bytes)
+                                         : st + planes * p.a_bytes;
+            const uint32_t b_lo = b_hi + p.b_bytes;
             const uint32_t d = tmem_base + (uint32_t)(grp * 16);
-            for (int ks = 0; ks < p.KS; ++ks) {
-              const uint32_t ao = (uint32_t)ks * 2 * a_lbo, bo = (uint32_t)ks * 2 * b_lbo;
-              tc_mma_f16_elect(d, smem_desc_kmajor(a_hi + ao, a_lbo, kSbo), smem_desc_kmajor(b_hi + bo, b_lbo, kSbo),
-                               p.idesc, ks > 0 ? 1u : 0u);
-              if (p.split) {
-                tc_mma_f16_elect(d, smem_desc_kmajor(a_hi + ao, a_lbo, kSbo), smem_desc_kmajor(b_lo + bo, b_lbo, kSbo),
-                                 p.idesc, 1u);
-                tc_mma_f16_elect(d, smem_desc_kmajor(a_lo + ao, a_lbo, kSbo), smem_desc_kmajor(b_hi + bo, b_lbo, kSbo),
-                                 p.idesc, 1u);
-              }
+            // descriptors of K-step 0; a K-step of 16 components advances the start
+            // address by 2 core-matrix columns (the low field counts 16-byte units)
+            const uint64_t ad = smem_desc_kmajor(a_hi, a_lbo, kSbo), bd = smem_desc_kmajor(b_hi, b_lbo, kSbo);
+            const uint64_t a_step = (2u * a_lbo) >> 4, b_step = (2u * b_lbo) >> 4;
+            const uint32_t leader = mma_leader;
+            if (!p.split) {
+              issue_group_rt<false>(p.KS, leader, d, ad, bd, 0, 0, a_step, b_step, p.idesc);
+            } else {
+              const uint64_t ad_lo = smem_desc_kmajor(a_lo, a_lbo, kSbo), bd_lo = smem_desc_kmajor(b_lo, b_lbo, kSbo);
+              issue_group_rt<true>(p.KS, leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, p.idesc);
             }
-            tc_commit_elect(&empty[s]);
+            tc_commit_by(leader, &empty[s]);
+            __syncwarp();
             ++it;
             if (++ms == p.stages) {
               ms = 0;
@@ -425,11 +521,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
             }
           }
           if (!ok) break;
-          tc_commit_elect(tmem_full);
+          tc_commit_by(mma_leader, tmem_full);
           ++tile;
         }
       }
-      tc_commit_elect(drain);  // every MMA complete before TMEM is released
+      tc_commit_by(mma_leader, drain);  // every MMA complete before TMEM is released
       mbar_wait_bounded(drain, 0, kTcBudget);
       __syncwarp();
     }
@@ -446,7 +542,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
       const int tp = unit % p.nTP, chunk = unit / p.nTP;
       const int rt0 = chunk * p.CH, rt1 = min(p.nRT, rt0 + p.CH);
       for (int rt = rt0; rt < rt1; ++rt, ++tile) {
-        const bool got = tc_wait(tmem_full, (uint32_t)(tile & 1), abort_flag, p.status);
+        const bool got = tc_wait(tmem_full, (uint32_t)(tile & 1), abort_flag, p.status, 128);
         __syncwarp();
         tc_fence_after();
         const long long n = (long long)rt * p.IPT + n_local;
@@ -519,22 +615,39 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   p.idesc = idesc_f16(precision == RSVD_FP16 ? 0u : 1u, 128, 16);
   p.a_bytes = (uint32_t)(kOpLanes * La.K * 2);
   p.b_bytes = (uint32_t)(16 * La.K * 2);
-  p.stage_bytes = (uint32_t)((planes * (p.a_bytes + p.b_bytes) + 1023) / 1024 * 1024);
   const uint32_t dense_bytes = (uint32_t)(planes * C::NT * kOpGroups * La.K * 2);  // per producer warp
   p.dense_bytes = dense_bytes;
   const uint32_t res_bytes = 2u * C::NT * kOpLanes * 16u;
   const uint32_t kMaxSmem = 227u * 1024u;
-  // two producer warps (each with its own template-row copy) while three or
-  // more stages still fit, else one
-  p.nprod = (kMaxSmem - (2u * dense_bytes + res_bytes + 1024u)) / p.stage_bytes >= 3 ? 2 : 1;
-  const uint32_t fixed = (uint32_t)p.nprod * dense_bytes + res_bytes + 1024u;
+  // Preferred layouts, first that fits: template blocks resident per unit
+  // (single-pass forms) with two producers, then one producer; else the blocks
+  // are rebuilt in every stage, two producers while three stages fit, else one.
+  const uint32_t bres_bytes = (uint32_t)kOpGroups * p.b_bytes;
+  struct Opt { int bres, nprod, min_stages; };
+  const Opt opts[] = {{1, 2, 3}, {1, 1, 3}, {0, 2, 3}, {0, 1, 2}};
+  bool found = false;
+  for (const Opt& o : opts) {
+    if (o.bres && planes != 1) continue;
+    const uint32_t sb = (uint32_t)((planes * (p.a_bytes + (o.bres ? 0u : p.b_bytes)) + 1023) / 1024 * 1024);
+    const uint32_t fx = (uint32_t)o.nprod * dense_bytes + (o.bres ? bres_bytes : 0u) + res_bytes + 1024u;
+    if (fx < kMaxSmem && (int)((kMaxSmem - fx) / sb) >= o.min_stages) {
+      p.bres = o.bres;
+      p.nprod = o.nprod;
+      p.stage_bytes = sb;
+      found = true;
+      break;
+    }
+  }
+  if (!found) return RSVD_EUNSUPPORTED;
+  const uint32_t fixed = (uint32_t)p.nprod * dense_bytes + (p.bres ? bres_bytes : 0u) + res_bytes + 1024u;
   int stages = (int)((kMaxSmem - fixed) / p.stage_bytes);
   if (stages > 6) stages = 6;
   uint32_t smem = 0;
   for (; stages >= 2; --stages) {
     p.stages = stages;
     p.dense_off = (uint32_t)stages * p.stage_bytes;
-    p.res_off = p.dense_off + (uint32_t)p.nprod * dense_bytes;
+    p.bres_off = p.dense_off + (uint32_t)p.nprod * dense_bytes;
+    p.res_off = p.bres_off + (p.bres ? bres_bytes : 0u);
     p.bar_off = p.res_off + res_bytes;
     smem = p.bar_off + (uint32_t)(2 * stages + 3) * 8u + 8u;
     if (smem < 120u * 1024u) smem = 120u * 1024u;  // one CTA (and one TMEM allocation) per SM

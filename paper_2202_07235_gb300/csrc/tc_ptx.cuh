@@ -66,6 +66,47 @@ __device__ __forceinline__ void tc_mma_f16_elect(uint32_t d_tmem, uint64_t a_des
       : "memory");
 }
 
+// 1 on one lane of the converged warp, 0 on the others.
+__device__ __forceinline__ uint32_t elect_one() {
+  uint32_t r;
+  asm volatile(
+      "{\n"
+      ".reg .pred e;\n"
+      "elect.sync _|e, 0xffffffff;\n"
+      "selp.u32 %0, 1, 0, e;\n"
+      "}\n"
+      : "=r"(r));
+  return r;
+}
+
+// MMA issued by the lane whose `leader` is non-zero; the warp computes the
+// (uniform) operands together.
+__device__ __forceinline__ void tc_mma_f16_by(uint32_t leader, uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p, e;\n"
+      "setp.ne.b32 e, %5, 0;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate), "r"(leader)
+      : "memory");
+}
+
+// tcgen05.commit tracks the MMAs of the executing thread: issue it from the
+// lane that issued them.
+__device__ __forceinline__ void tc_commit_by(uint32_t leader, uint64_t* bar) {
+  asm volatile(
+      "{\n"
+      ".reg .pred e;\n"
+      "setp.ne.b32 e, %1, 0;\n"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+      "}\n" ::"r"(smem_addr(bar)),
+      "r"(leader)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_commit_elect(uint64_t* bar) {
   asm volatile(
       "{\n"
@@ -181,6 +222,72 @@ __device__ __forceinline__ void tmem_ld_pair<4>(uint32_t ta, uint32_t tb, float2
     a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
     b[i] = make_float2(__uint_as_float(r[8 + 2 * i]), __uint_as_float(r[8 + 2 * i + 1]));
   }
+}
+
+// Split forms of the loads above for overlapping them with arithmetic: the
+// issue returns at once, and tmem_wait_ld_tie(r) waits for every load of the
+// thread while naming `r` as its output, so no use of `r` can be placed before
+// the wait.
+template <int N>
+__device__ __forceinline__ void tmem_ld_pair_issue(uint32_t ta, uint32_t tb, uint32_t (&r)[4 * N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld_pair_issue<2>(uint32_t ta, uint32_t tb, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%8];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%9];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(ta), "r"(tb)
+      : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld_pair_issue<4>(uint32_t ta, uint32_t tb, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+}
+
+// Eight loads of 2 columns at taddr + i * stride, no wait.
+__device__ __forceinline__ void tmem_ld2x8_issue(uint32_t taddr, uint32_t stride, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%17];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%18];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%19];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%20];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%21];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%22];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14, %15}, [%23];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr), "r"(taddr + stride), "r"(taddr + 2 * stride), "r"(taddr + 3 * stride),
+        "r"(taddr + 4 * stride), "r"(taddr + 5 * stride), "r"(taddr + 6 * stride), "r"(taddr + 7 * stride)
+      : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_wait_ld_tie(uint32_t (&r)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_wait_ld_tie<8>(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_wait_ld_tie<16>(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 // Registers -> TMEM: `N` complex values (2N columns) at taddr. The caller
