@@ -226,3 +226,40 @@ def test_operand_forms_reject_unsupported_sizes():
     with pytest.raises(P.RSVDError):  # split operands at Q = 256: shared memory holds H <= 18
         P.align_best(x, 1, 1, x, 1, 20, 256, precision="bf16x3")
     assert P.compressed_bytes(4, 1, 8, 64, "bf16") == 0
+
+
+def test_precision_study():
+    """Relative error on X and argmax agreement of every operand form against the
+    FP64 oracle: 64 px images, 32 rings, Q = 128, 256 images x 64 templates
+    (SNR 0.1, seed 0), H in {8, 12, 16, 24}. The table is printed (pytest -s)."""
+    from synthetic import CONFIGS
+
+    cfg = dict(CONFIGS["precision"])
+    rows = []
+    for H in (8, 12, 16, 24):
+        wl, A, B, U = setup(N=cfg["N"], R=cfg["R"], Q=cfg["Q"], N_B=cfg["N_B"], N_A=cfg["N_A"], H=H,
+                            snr=cfg["snr"], seed=0)
+        g = wl.grid
+        Q = cfg["Q"]
+        a = O.compress(O.translate(A.astype(np.complex128), g.k, wl.deltas), U, g.w)
+        b = O.compress(B.astype(np.complex128), U, g.w)
+        Xr = O.scores_compressed(a, b).real
+        rb, ra = O.align_best(Xr)
+        Ut = torch.from_numpy(U).to(DEV)
+        At, Bt = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
+        truth = ra[np.arange(cfg["N_A"]), wl.truth_j] == wl.truth_m  # oracle recovers the rotation
+        for form in ("fp32", "bf16", "fp16", "bf16x3"):
+            cA = P.compress(g.k, g.w, Ut, At, precision=form)
+            cB = P.compress(g.k, g.w, Ut, Bt, precision=form)
+            X = P.align_scores(cA, cfg["N_A"], 1, cB, cfg["N_B"], H, Q, precision=form).cpu().numpy().astype(np.float64)
+            best, arg, _ = P.align_best(cA, cfg["N_A"], 1, cB, cfg["N_B"], H, Q, precision=form)
+            P.status()
+            arg = arg.cpu().numpy()
+            rel_f = np.linalg.norm(X - Xr) / np.linalg.norm(Xr)
+            rows.append((H, form, rel_f, _pair_scale_err(X, Xr), float(np.mean(arg == ra)),
+                         float(np.mean(arg[np.arange(cfg["N_A"]), wl.truth_j] == wl.truth_m)), float(np.mean(truth))))
+            bound = {"fp32": 1e-5, "bf16x3": 1e-5, "fp16": 1e-3, "bf16": 5e-3}[form]
+            assert rel_f <= bound, (H, form, rel_f)
+    print("\nH  form    relF(X)    max pair-rel  argmax=oracle  rotation recovered (form / oracle)")
+    for H, form, rf, pe, agree, rec, rec_o in rows:
+        print(f"{H:<2} {form:<7} {rf:.3e}  {pe:.3e}     {agree:.5f}        {rec:.4f} / {rec_o:.4f}")
