@@ -33,5 +33,6 @@ from .rsvd_ref import (  # noqa: F401
     scores_compressed_form,
     scores_direct,
     scores_fb,
+    scores_fine,
     translate,
 )

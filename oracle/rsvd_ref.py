@@ -284,3 +284,24 @@ def scores_compressed_form(a_c: np.ndarray, b_c: np.ndarray, form: str) -> np.nd
     `form`: X_hat = 2 pi sum over terms of sum_h conj(A) B, X = forward DFT."""
     Xhat = sum(2.0 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(A), B) for A, B in operand_terms(a_c, b_c, form))
     return np.fft.fft(Xhat, axis=-1).real
+
+
+# ---------------------------------------------------------------------------
+# Section 2.3 (after eq. image_innerproduct): a finer rotation grid by
+# zero-padding X_hat before the transform over q. The padded transform is the
+# trigonometric interpolant of the real landscape; the Nyquist coefficient
+# q = Q/2 is shared equally by q = +Q/2 and q = -Q/2 so that the interpolant is
+# real and takes the values X(gamma_m) at the Q coarse angles.
+# ---------------------------------------------------------------------------
+def scores_fine(a_c: np.ndarray, b_c: np.ndarray, P: int) -> np.ndarray:
+    """Real X [nA, T, nB, P Q] at gamma = 2 pi m' / (P Q), m' = 0..PQ-1:
+    X(gamma) = sum_{|q| < Q/2} X_hat(q mod Q) e^{-i q gamma} + X_hat(Q/2) cos(Q gamma / 2),
+    X_hat of Step 1 (eq. image_innerproduct_pm), evaluated as a direct sum."""
+    Q = a_c.shape[-1]
+    Xhat = 2.0 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(a_c), b_c)
+    gamma = 2.0 * math.pi * np.arange(P * Q) / (P * Q)
+    q = np.arange(-(Q // 2) + 1, Q // 2)
+    E = np.exp(-1j * np.outer(q, gamma))  # [2Q/2 - 1, PQ]
+    X = np.einsum("ntjq,qm->ntjm", Xhat[..., q % Q], E)
+    X = X + Xhat[..., Q // 2][..., None] * np.cos(0.5 * Q * gamma)
+    return X.real

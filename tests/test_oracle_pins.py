@@ -253,3 +253,55 @@ def test_lse_partials_and_loss_match_definition():
     assert abs(loss - Ln.sum()) < 1e-12
     # the per-image loss is the log-sum-exp of the per-pair partials
     assert np.allclose(logsumexp(P, axis=1), Ln, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Finer rotation grid by zero-padding X_hat (section 2.3).
+# ---------------------------------------------------------------------------
+def test_fine_grid_takes_the_coarse_values_at_coarse_angles():
+    wl = make_workload(N=32, R=16, Q=32, N_B=3, N_A=4, snr=0.3, T_side=2, seed=31)
+    g = wl.grid
+    U, _ = O.principal_vectors(O.radial_kernel(wl.templates, g.w), 8)
+    a = O.compress(O.translate(wl.images, g.k, wl.deltas), U, g.w)
+    b = O.compress(wl.templates, U, g.w)
+    X = O.scores_compressed(a, b).real
+    for P in (1, 2, 4):
+        Xf = O.scores_fine(a, b, P)
+        assert Xf.shape[-1] == P * 32
+        assert np.allclose(Xf[..., ::P], X, rtol=0, atol=1e-12 * np.abs(X).max())
+
+
+def test_fine_grid_nyquist_term_is_a_real_cosine():
+    Q, H, P = 16, 3, 4
+    a = np.zeros((1, 1, H, Q), dtype=complex)
+    b = np.zeros((1, H, Q), dtype=complex)
+    a[..., Q // 2] = 1.0
+    b[..., Q // 2] = 1.0
+    gamma = 2 * math.pi * np.arange(P * Q) / (P * Q)
+    ref = 2 * math.pi * H * np.cos(0.5 * Q * gamma)
+    assert np.allclose(O.scores_fine(a, b, P)[0, 0, 0], ref, atol=1e-12)
+
+
+def test_fine_grid_matches_the_definition_at_an_off_grid_rotation():
+    """Image = template rotated analytically by a half-grid angle gamma0: the
+    fine landscape's maximum sits at gamma0 and equals the direct polar-quadrature
+    inner product <A, R_gamma0 B> of the definition (section 2.2)."""
+    from synthetic.inputs import blobs_polar_ft, draw_blobs, polar_grid
+
+    N, R, Q, P = 64, 32, 128, 2
+    grid = polar_grid(N, R, Q)
+    rng = np.random.default_rng(5)
+    blobs = draw_blobs(rng, 1)
+    m0 = 37
+    gamma0 = 2 * math.pi * (m0 + 0.5) / Q
+    B = blobs_polar_ft(grid, blobs)
+    A = blobs_polar_ft(grid, blobs, rotation=np.array([gamma0]))
+    U, _ = O.principal_vectors(O.radial_kernel(B, grid.w), R)
+    a = O.compress(A[:, None], U, grid.w)
+    b = O.compress(B, U, grid.w)
+    Xf = O.scores_fine(a, b, P)[0, 0, 0]
+    # definition at gamma0: <A, R_gamma0 B> with R_gamma0 B the analytically rotated template
+    B_rot = blobs_polar_ft(grid, blobs, rotation=np.array([gamma0]))
+    direct = float(np.real(np.sum(grid.w[:, None] * np.conj(A[0]) * B_rot[0])) * grid.dpsi)
+    assert int(np.argmax(Xf)) == 2 * m0 + 1
+    assert abs(Xf[2 * m0 + 1] - direct) <= 1e-8 * abs(direct)
