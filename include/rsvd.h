@@ -240,6 +240,40 @@ int rsvd_compress_backward(int R, int Q, const double* k, const double* w, const
                            const void* gC, int N, const double* deltas, int T, int precision,
                            void* gpolar, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Finer rotation grid (section 2.4, after eq. image_innerproduct: X_hat
+ * zero-padded before the transform over q). The landscape on P Q angles
+ * gamma = 2 pi m' / (P Q) is the trigonometric interpolant
+ *   X(gamma) = sum_{|q| < Q/2} X_hat(q) e^{-i q gamma} + X_hat(Q/2) cos(Q gamma / 2),
+ * which equals X(gamma_m) at the Q coarse angles (m' = P m). P in {1, 2, 4, 8},
+ * P Q <= 1024, RSVD_FP32 only (else RSVD_EUNSUPPORTED); generic per-pair kernel.
+ *
+ * rsvd_align_scores_fine: X dev float [N_A][T][N_B][P Q].
+ * rsvd_align_best_fine:   as rsvd_align_best with arg = t P Q + m'.
+ * rsvd_align_best_pairs:  the same for an explicit list of K (image, template)
+ *   pairs, dev int32 [K][2] (8-byte aligned); best, arg, lse dev [K]. A pair
+ *   outside [0, N_A) x [0, N_B) leaves its outputs unwritten and records
+ *   RSVD_EDEVICE in the status word.
+ * ------------------------------------------------------------------------ */
+int rsvd_align_scores_fine(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int P,
+                           int precision, float* X, void* stream);
+int rsvd_align_best_fine(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int P,
+                         int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
+                         void* stream);
+int rsvd_align_best_pairs(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int P,
+                          int precision, const int32_t* pairs, int K, float inv_sigma2, float* best,
+                          int32_t* arg, float* lse, void* stream);
+
+/* Candidate selection for principal-mode-marching (section 5, discussion: a
+ * coarse landscape at a low rank H, then the promising candidates refined at a
+ * higher rank). For each image n, the `keep` templates with the largest
+ * best[n][j] (equal scores in increasing j) as pairs (n, j), written to rows
+ * n*keep .. n*keep + keep - 1 of `pairs` in decreasing score.
+ *   best   dev float [N_A][N_B] (e.g. from rsvd_align_best at the low rank)
+ *   keep   1 .. min(N_B, 64) (else RSVD_EUNSUPPORTED)
+ *   pairs  dev int32 [N_A * keep][2] -- output, for rsvd_align_best_pairs */
+int rsvd_select_pairs(const float* best, int N_A, int N_B, int keep, int32_t* pairs, void* stream);
+
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).
  * Provided so callers can cross-check the fused kernel. */

@@ -287,7 +287,7 @@ def scores_compressed_form(a_c: np.ndarray, b_c: np.ndarray, form: str) -> np.nd
 
 
 # ---------------------------------------------------------------------------
-# Section 2.3 (after eq. image_innerproduct): a finer rotation grid by
+# Section 2.4 (after eq. image_innerproduct): a finer rotation grid by
 # zero-padding X_hat before the transform over q. The padded transform is the
 # trigonometric interpolant of the real landscape; the Nyquist coefficient
 # q = Q/2 is shared equally by q = +Q/2 and q = -Q/2 so that the interpolant is

@@ -11,7 +11,11 @@ from .api import (  # noqa: F401
     PRECISIONS,
     LSEAlign,
     align_best,
+    align_best_fine,
+    align_best_pairs,
+    align_marching,
     align_scores,
+    align_scores_fine,
     build_radial_svd,
     build_radial_svd_noalloc,
     build_workspace_bytes,
@@ -22,5 +26,6 @@ from .api import (  # noqa: F401
     lse_backward,
     lse_rows,
     pack,
+    select_pairs,
     status,
 )

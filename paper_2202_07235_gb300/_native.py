@@ -44,6 +44,13 @@ SIGNATURES = {
     "rsvd_align_best_pairwise": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float,
                                          c_void_p, c_void_p, c_void_p, c_void_p]),
     "rsvd_pack": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "rsvd_align_scores_fine": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
+                                       c_void_p]),
+    "rsvd_align_best_fine": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_float,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rsvd_align_best_pairs": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
+                                      c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rsvd_select_pairs": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
 }
 
 

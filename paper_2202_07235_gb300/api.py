@@ -168,6 +168,67 @@ def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H
     return best, arg, lse
 
 
+def align_scores_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int, P: int,
+                      stream=None) -> torch.Tensor:
+    """Landscape on the P-times finer rotation grid, float32 [N_A, T, N_B, P*Q]."""
+    X = torch.empty((N_A, T, N_B, P * Q), dtype=torch.float32, device=cA.device)
+    check(lib().rsvd_align_scores_fine(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, FP32, _ptr(X), _stream(stream)),
+          "rsvd_align_scores_fine")
+    return X
+
+
+def align_best_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int, P: int,
+                    inv_sigma2: float = 1.0, want_lse: bool = False, stream=None):
+    """best / arg (t*P*Q + m') / lse on the P-times finer rotation grid."""
+    dev = cA.device
+    best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
+    arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
+    lse = torch.empty((N_A, N_B), dtype=torch.float32, device=dev) if want_lse else None
+    check(lib().rsvd_align_best_fine(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, FP32, float(inv_sigma2), _ptr(best),
+                                     _ptr(arg), _ptr(lse) if lse is not None else None, _stream(stream)),
+          "rsvd_align_best_fine")
+    return best, arg, lse
+
+
+def align_best_pairs(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int,
+                     pairs: torch.Tensor, P: int = 1, inv_sigma2: float = 1.0, want_lse: bool = False, stream=None):
+    """best / arg / lse for the (image, template) pairs int32 [K, 2]."""
+    _require_cuda(pairs, torch.int32, "pairs")
+    K = pairs.shape[0]
+    dev = cA.device
+    best = torch.empty((K,), dtype=torch.float32, device=dev)
+    arg = torch.empty((K,), dtype=torch.int32, device=dev)
+    lse = torch.empty((K,), dtype=torch.float32, device=dev) if want_lse else None
+    check(lib().rsvd_align_best_pairs(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, FP32, _ptr(pairs), K,
+                                      float(inv_sigma2), _ptr(best), _ptr(arg),
+                                      _ptr(lse) if lse is not None else None, _stream(stream)),
+          "rsvd_align_best_pairs")
+    return best, arg, lse
+
+
+def select_pairs(best: torch.Tensor, keep: int, stream=None) -> torch.Tensor:
+    """Per image, the `keep` best templates as int32 pairs [N_A*keep, 2]."""
+    _require_cuda(best, torch.float32, "best")
+    N_A, N_B = best.shape
+    pairs = torch.empty((N_A * keep, 2), dtype=torch.int32, device=best.device)
+    check(lib().rsvd_select_pairs(_ptr(best), N_A, N_B, keep, _ptr(pairs), _stream(stream)), "rsvd_select_pairs")
+    return pairs
+
+
+def align_marching(coarse, fine, N_A: int, T: int, N_B: int, Q: int, keep: int, P: int = 1, stream=None):
+    """Principal-mode-marching (section 5): align at a low rank, keep each image's
+    `keep` best templates, rescore those pairs at a higher rank (optionally on a
+    P-times finer rotation grid). coarse = (cA, cB, H) and fine = (cA, cB, H) are
+    compressed rings at the two ranks. Returns (pairs [N_A*keep, 2], best, arg) of
+    the refined pass and the coarse (best, arg)."""
+    cA0, cB0, H0 = coarse
+    cA1, cB1, H1 = fine
+    b0, a0, _ = align_best(cA0, N_A, T, cB0, N_B, H0, Q, stream=stream)
+    pairs = select_pairs(b0, keep, stream=stream)
+    b1, a1, _ = align_best_pairs(cA1, N_A, T, cB1, N_B, H1, Q, pairs, P=P, stream=stream)
+    return pairs, b1, a1, (b0, a0)
+
+
 def lse_rows(lse: torch.Tensor, stream=None) -> torch.Tensor:
     """L[n] = log sum_j exp(lse[n][j])."""
     N_A, N_B = lse.shape

@@ -256,7 +256,7 @@ def test_lse_partials_and_loss_match_definition():
 
 
 # ---------------------------------------------------------------------------
-# Finer rotation grid by zero-padding X_hat (section 2.3).
+# Finer rotation grid by zero-padding X_hat (section 2.4).
 # ---------------------------------------------------------------------------
 def test_fine_grid_takes_the_coarse_values_at_coarse_angles():
     wl = make_workload(N=32, R=16, Q=32, N_B=3, N_A=4, snr=0.3, T_side=2, seed=31)
