@@ -27,6 +27,7 @@ from .rsvd_ref import (  # noqa: F401
     operand_terms,
     principal_vectors,
     radial_kernel,
+    radial_kernel_translated,
     round_bf16,
     round_fp16,
     scores_compressed,
@@ -35,4 +36,5 @@ from .rsvd_ref import (  # noqa: F401
     scores_fb,
     scores_fine,
     translate,
+    translation_moments,
 )

@@ -305,3 +305,55 @@ def scores_fine(a_c: np.ndarray, b_c: np.ndarray, P: int) -> np.ndarray:
     X = np.einsum("ntjq,qm->ntjm", Xhat[..., q % Q], E)
     X = X + Xhat[..., Q // 2][..., None] * np.cos(0.5 * Q * gamma)
     return X.real
+
+
+# ---------------------------------------------------------------------------
+# Section 5 (discussion), eq. Image_single_cost_with_translations: the
+# principal vectors of the objective that averages over a distribution of
+# rotations (uniform on the Q grid angles) and of translations mu_delta (here
+# a weighted discrete set) of the target,
+#   C(u; B) = E E' sum_psi | [u^T T_d R_g B](psi) - [u^T T_d' R_g' B](psi) |^2 ,
+# is quadratic in u. With b_{d,g}(r, psi) = sqrt(w_r) B(k_r, psi - g) exp(-i k_r d.n(psi)),
+#   C(u; B) = 2 Q u^T K u,  K_{rr'} = (1/Q) sum_psi Re[ E conj(b_r) b_r' - conj(E b_r) E b_r' ].
+# With delta = 0 only, K is the kernel of section 3.3 (q = 0 excluded).
+# ---------------------------------------------------------------------------
+def radial_kernel_translated(B: np.ndarray, w: np.ndarray, k: np.ndarray, deltas: np.ndarray,
+                             weights: np.ndarray | None = None) -> np.ndarray:
+    """K averaged over the templates B [nB, R, Q] (mean over j as in eq.
+    image_cost_and_kern), by explicit expectation over the Q rotations g of the
+    grid and the translations deltas [T, 2] with probabilities `weights`."""
+    nB, R, Q = B.shape
+    T = deltas.shape[0]
+    p = np.full(T, 1.0 / T) if weights is None else np.asarray(weights, float) / np.sum(weights)
+    psi = 2.0 * math.pi * np.arange(Q) / Q
+    proj = deltas[:, 0][:, None] * np.cos(psi)[None, :] + deltas[:, 1][:, None] * np.sin(psi)[None, :]
+    phase = np.exp(-1j * k[None, :, None] * proj[:, None, :])  # [T, R, Q]
+    eta = np.sqrt(w)
+    K = np.zeros((R, R))
+    for j in range(nB):
+        M2 = np.zeros((R, R), dtype=complex)
+        m = np.zeros((R, Q), dtype=complex)
+        for g in range(Q):
+            rot = np.roll(B[j], g, axis=-1)  # B(k_r, psi - gamma_g)
+            for t in range(T):
+                b = eta[:, None] * rot * phase[t]  # [R, Q]
+                M2 += (p[t] / Q) * (np.conj(b) @ b.T)  # sum over psi
+                m += (p[t] / Q) * b
+        K += (M2 - np.conj(m) @ m.T).real / Q
+    return K / nB
+
+
+def translation_moments(k: np.ndarray, deltas: np.ndarray, weights: np.ndarray | None, Q: int):
+    """Phi_{rr'} = (1/Q) sum_psi E_d exp(i (k_r - k_r') d.n(psi)) and
+    Psi_{rr'} = (1/Q) sum_psi conj(phi_r(psi)) phi_r'(psi), phi_r(psi) = E_d exp(-i k_r d.n(psi)):
+    the translation averages in K = sqrt(w w') [S Phi - b0 b0 Psi] (S_j: the
+    Parseval sum over all q of template j, b0: its ring means)."""
+    T = deltas.shape[0]
+    p = np.full(T, 1.0 / T) if weights is None else np.asarray(weights, float) / np.sum(weights)
+    psi = 2.0 * math.pi * np.arange(Q) / Q
+    proj = deltas[:, 0][:, None] * np.cos(psi)[None, :] + deltas[:, 1][:, None] * np.sin(psi)[None, :]  # [T, Q]
+    dk = k[:, None] - k[None, :]
+    Phi = np.einsum("t,rstq->rs", p, np.exp(1j * dk[:, :, None, None] * proj[None, None])) / Q
+    phi = np.einsum("t,rtq->rq", p, np.exp(-1j * k[:, None, None] * proj[None]))
+    Psi = (np.conj(phi) @ phi.T) / Q
+    return Phi, Psi
