@@ -106,6 +106,28 @@ int rsvd_build_radial_svd(int R, int Q, const double* w, const void* templates, 
                           double* U, double* eig, void* workspace, size_t workspace_bytes,
                           void* stream);
 
+/* Translation-aware form (section 5, eq. Image_single_cost_with_translations:
+ * the objective averaged over the Q grid rotations and a distribution of
+ * translations of each template). Its kernel, in FP64 on the device:
+ *   C_{rr'} = sqrt(w_r w_r') / N_B sum_j [ S_j(r,r') Phi_{rr'} - b_j(k_r,0) b_j(k_r',0) Psi_{rr'} ]
+ *   S_j(r,r') = sum_q conj(b_j(k_r,q)) b_j(k_r',q)  (all q),
+ *   Phi_{rr'} = (1/Q) sum_psi sum_t p_t cos((k_r - k_r') delta_t . n(psi)),
+ *   Psi_{rr'} = (1/Q) sum_psi Re conj(phi_r(psi)) phi_r'(psi),
+ *   phi_r(psi) = sum_t p_t exp(-i k_r delta_t . n(psi)),  n(psi) = (cos psi, sin psi);
+ * with the single translation 0 it equals the kernel of rsvd_build_radial_svd.
+ * For an isotropic Gaussian translation density of deviation sigma, Phi
+ * tends to the paper's E+(k_r, k_r') = exp(-sigma^2 (k_r^2 + k_r'^2) / 2) exp(k_r k_r' sigma^2).
+ *   k          host double[R] ring radii
+ *   deltas     host double [T][2] translations (image units), T = 1..64
+ *   weights    host double [T] probabilities (normalised here; NULL = uniform), >= 0
+ *   workspace  dev, >= rsvd_build_translated_workspace_bytes(R, Q, N_B) bytes, 256-byte aligned
+ * Other arguments and results as rsvd_build_radial_svd. */
+size_t rsvd_build_translated_workspace_bytes(int R, int Q, int N_B);
+int rsvd_build_radial_svd_translated(int R, int Q, const double* k, const double* w, const void* templates,
+                                     int N_B, const double* deltas, const double* weights, int T, int H,
+                                     double* U, double* eig, void* workspace, size_t workspace_bytes,
+                                     void* stream);
+
 /* Allocation-free form of rsvd_build_radial_svd (the paper has no
  * counterpart; it is a memory-management variant of the call above).
  * For callers that cannot allocate device memory: code that receives only

@@ -18,6 +18,7 @@ from .api import (  # noqa: F401
     align_scores_fine,
     build_radial_svd,
     build_radial_svd_noalloc,
+    build_radial_svd_translated,
     build_workspace_bytes,
     compress,
     compress_backward,

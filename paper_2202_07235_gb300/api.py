@@ -89,6 +89,32 @@ def build_radial_svd_noalloc(w, templates: torch.Tensor, H: int, stream=None):
     return U, eig
 
 
+def build_radial_svd_translated(k, w, templates: torch.Tensor, H: int, deltas, weights=None, stream=None):
+    """Principal vectors of the translation-aware kernel (translations deltas
+    (T, 2) with probabilities `weights`, uniform if None). Returns (U, eig)."""
+    _require_cuda(templates, torch.complex64, "templates")
+    N_B, R, Q = templates.shape
+    ka, kp = _host_f64(k)
+    wa, wp = _host_f64(w)
+    da, dp = _host_f64(deltas)
+    T = da.reshape(-1, 2).shape[0]
+    if weights is None:
+        wt = None
+    else:
+        wta, wt = _host_f64(weights)
+        if wta.shape != (T,):
+            raise ValueError("weights must have length T")
+    dev = templates.device
+    U = torch.empty((R, H), dtype=torch.float64, device=dev)
+    eig = torch.empty((R,), dtype=torch.float64, device=dev)
+    need = int(lib().rsvd_build_translated_workspace_bytes(R, Q, N_B))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    check(lib().rsvd_build_radial_svd_translated(R, Q, kp, wp, _ptr(templates), N_B, dp, wt, T, H, _ptr(U), _ptr(eig),
+                                                 _ptr(ws), ws.numel(), _stream(stream)),
+          "rsvd_build_radial_svd_translated")
+    return U, eig
+
+
 def compressed_bytes(N: int, T: int, H: int, Q: int, precision=FP32) -> int:
     return int(lib().rsvd_compressed_bytes(N, T, H, Q, _prec(precision)))
 

@@ -55,6 +55,9 @@ BuildPlan make_plan(int R, int N_B) {
   return pl;
 }
 
+// kSplit: the two sums are kept apart (partial = sum_j (2/Q) G_j, partial + nslices R^2 =
+// sum_j m_j m_j^T) for the translation-aware kernel, which weighs them differently.
+template <bool kSplit>
 __global__ void __launch_bounds__(kThreads) kernel_partial(const float2* __restrict__ B, int N_B, int R, int Q,
                                                            int tiles1d, int nslices, double* __restrict__ partial) {
   __shared__ float2 sr[kTile][kPsiChunk + 1];
@@ -67,11 +70,11 @@ __global__ void __launch_bounds__(kThreads) kernel_partial(const float2* __restr
   const int j_begin = (int)((long long)N_B * slice / nslices);
   const int j_end = (int)((long long)N_B * (slice + 1) / nslices);
   const double scale_g = 2.0 / (double)Q;
-  double acc[4][4];
+  double acc[4][4], acc2[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = acc2[a][b] = 0.0;
 
   for (int j = j_begin; j < j_end; ++j) {
     const float2* Bj = B + (size_t)j * R * Q;
@@ -114,17 +117,27 @@ __global__ void __launch_bounds__(kThreads) kernel_partial(const float2* __restr
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b)
-        acc[a][b] += scale_g * g[a][b] - (scale_g * mr[a]) * (scale_g * mc[b]);
+      for (int b = 0; b < 4; ++b) {
+        if (kSplit) {
+          acc[a][b] += scale_g * g[a][b];
+          acc2[a][b] += (scale_g * mr[a]) * (scale_g * mc[b]);
+        } else {
+          acc[a][b] += scale_g * g[a][b] - (scale_g * mr[a]) * (scale_g * mc[b]);
+        }
+      }
   }
   double* out = partial + (size_t)slice * R * R;
+  double* out2 = partial + ((size_t)nslices + slice) * R * R;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int r = r0 + ty * 4 + a;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int c = c0 + tx * 4 + b;
-      if (r < R && c < R) out[(size_t)r * R + c] = acc[a][b];
+      if (r < R && c < R) {
+        out[(size_t)r * R + c] = acc[a][b];
+        if (kSplit) out2[(size_t)r * R + c] = acc2[a][b];
+      }
     }
   }
 }
@@ -291,8 +304,8 @@ extern "C" int rsvd_build_radial_svd(int R, int Q, const double* w, const void* 
   double* V = reinterpret_cast<double*>(ws + pl.off_V);
 
   dim3 grid(pl.nslices, pl.ntiles);
-  kernel_partial<<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.tiles1d, pl.nslices,
-                                            partial);
+  kernel_partial<false><<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.tiles1d,
+                                                   pl.nslices, partial);
   if ((rc = launch_status()) != RSVD_OK) return rc;
   ReduceParams rp{};
   rp.partial = partial;
@@ -405,8 +418,8 @@ extern "C" int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, cons
   double* V = reinterpret_cast<double*>(ws + pl.off_V);
 
   dim3 grid(pl.nslices, pl.ntiles);
-  kernel_partial<<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.tiles1d, pl.nslices,
-                                            partial);
+  kernel_partial<false><<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.tiles1d,
+                                                   pl.nslices, partial);
   if ((rc = launch_status()) != RSVD_OK) return rc;
   rp.partial = partial;
   rp.C = C;
@@ -414,6 +427,227 @@ extern "C" int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, cons
   rp.nslices = pl.nslices;
   rp.N_B = N_B;
   kernel_reduce<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  const size_t need = (size_t)2 * R * R * sizeof(double);
+  const int use_smem = need <= 160 * 1024 ? 1 : 0;
+  const size_t smem = use_smem ? need : 0;
+  if (use_smem &&
+      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RSVD_ECUDA;
+  jacobi_eig<<<1, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
+  return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Translation-aware kernel (section 5, eq. Image_single_cost_with_translations):
+// the objective averaged over the Q grid rotations and a distribution of
+// translations {delta_t, p_t} of the target is quadratic in u with kernel
+//   C_{rr'} = sqrt(w_r w_r') / N_B * sum_j [ S_j(r,r') Phi_{rr'} - m_j(r) m_j(r') Psi_{rr'} ],
+//   S_j(r,r')  = sum_q conj(b_j(r,q)) b_j(r',q)   (all q; Parseval on each ring),
+//   m_j(r)     = b_j(r,0)                         (ring mean),
+//   Phi_{rr'}  = (1/Q) sum_psi sum_t p_t cos((k_r - k_r') delta_t.n(psi)),
+//   Psi_{rr'}  = (1/Q) sum_psi Re conj(phi_r(psi)) phi_r'(psi),  phi_r(psi) = sum_t p_t exp(-i k_r delta_t.n(psi)),
+// (real parts: S_j and m_j are real for the transform of a real image). With the
+// single translation delta = 0 it is the kernel of rsvd_build_radial_svd.
+// ---------------------------------------------------------------------------
+namespace rsvd {
+namespace {
+
+constexpr int kMomTile = 16;
+constexpr int kMomChunk = 32;
+
+struct MomentParams {
+  double k[kMaxR];
+  double dx[kMaxT], dy[kMaxT], pt[kMaxT];
+  int R, Q, T;
+};
+
+// phi[r][q] = sum_t p_t exp(-i k_r rho_t(q)), rho_t(q) = dx_t cos psi_q + dy_t sin psi_q.
+__global__ void kernel_phi(const __grid_constant__ MomentParams p, double2* __restrict__ phi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.R * p.Q) return;
+  const int r = i / p.Q, q = i % p.Q;
+  double sp, cp;
+  sincospi(2.0 * q / p.Q, &sp, &cp);
+  double re = 0.0, im = 0.0;
+  for (int t = 0; t < p.T; ++t) {
+    double s, c;
+    sincos(p.k[r] * (p.dx[t] * cp + p.dy[t] * sp), &s, &c);
+    re += p.pt[t] * c;
+    im -= p.pt[t] * s;
+  }
+  phi[i] = make_double2(re, im);
+}
+
+// Phi and Psi on 16 x 16 tiles of (r, r'); exp(-i k rho) of the tile's rows and
+// columns is staged per (translation, chunk of angles) in shared memory.
+__global__ void __launch_bounds__(kMomTile * kMomTile) kernel_moments(const __grid_constant__ MomentParams p,
+                                                                     const double2* __restrict__ phi,
+                                                                     double* __restrict__ Phi,
+                                                                     double* __restrict__ Psi) {
+  __shared__ double2 er[kMomTile][kMomChunk + 1], ec[kMomTile][kMomChunk + 1];
+  __shared__ double cps[kMomChunk], sps[kMomChunk];
+  const int tiles1d = (p.R + kMomTile - 1) / kMomTile;
+  const int r0 = (blockIdx.x / tiles1d) * kMomTile, c0 = (blockIdx.x % tiles1d) * kMomTile;
+  const int ty = threadIdx.x / kMomTile, tx = threadIdx.x % kMomTile;
+  const int r = r0 + ty, c = c0 + tx;
+  double acc = 0.0;
+  for (int t = 0; t < p.T; ++t) {
+    for (int q0 = 0; q0 < p.Q; q0 += kMomChunk) {
+      __syncthreads();
+      if (threadIdx.x < kMomChunk) {
+        double sp = 0.0, cp = 0.0;
+        if (q0 + threadIdx.x < p.Q) sincospi(2.0 * (q0 + threadIdx.x) / p.Q, &sp, &cp);
+        cps[threadIdx.x] = cp;
+        sps[threadIdx.x] = sp;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < 2 * kMomTile * kMomChunk; i += blockDim.x) {
+        const int side = i / (kMomTile * kMomChunk), rem = i % (kMomTile * kMomChunk);
+        const int row = rem / kMomChunk, qq = rem % kMomChunk;
+        const int rr = (side == 0 ? r0 : c0) + row;
+        double2 e = make_double2(0.0, 0.0);
+        if (rr < p.R && q0 + qq < p.Q) {
+          double s, cc;
+          sincos(p.k[rr] * (p.dx[t] * cps[qq] + p.dy[t] * sps[qq]), &s, &cc);
+          e = make_double2(cc, -s);
+        }
+        if (side == 0)
+          er[row][qq] = e;
+        else
+          ec[row][qq] = e;
+      }
+      __syncthreads();
+      double part = 0.0;
+#pragma unroll 8
+      for (int qq = 0; qq < kMomChunk; ++qq) part += er[ty][qq].x * ec[tx][qq].x + er[ty][qq].y * ec[tx][qq].y;
+      acc += p.pt[t] * part;
+    }
+  }
+  if (r < p.R && c < p.R) {
+    double ps = 0.0;
+    for (int q = 0; q < p.Q; ++q) {
+      const double2 a = phi[(size_t)r * p.Q + q], b = phi[(size_t)c * p.Q + q];
+      ps += a.x * b.x + a.y * b.y;
+    }
+    Phi[(size_t)r * p.R + c] = acc / p.Q;
+    Psi[(size_t)r * p.R + c] = ps / p.Q;
+  }
+}
+
+struct ReduceTParams {
+  const double* partial;  // [2 nslices][R][R]
+  const double* Phi;
+  const double* Psi;
+  double* C;
+  int R, nslices, N_B;
+  double sw[kMaxR];
+};
+
+__global__ void kernel_reduce_translated(const __grid_constant__ ReduceTParams p) {
+  const int RR = p.R * p.R;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < RR; i += gridDim.x * blockDim.x) {
+    double g = 0.0, m = 0.0;
+    for (int k = 0; k < p.nslices; ++k) {
+      g += p.partial[(size_t)k * RR + i];
+      m += p.partial[((size_t)p.nslices + k) * RR + i];
+    }
+    const int r = i / p.R, c = i % p.R;
+    p.C[i] = (g * p.Phi[i] - m * p.Psi[i]) * p.sw[r] * p.sw[c] / (double)p.N_B;
+  }
+}
+
+struct BuildTPlan {
+  BuildPlan base;
+  size_t off_Phi, off_Psi, off_phi, total;
+};
+
+BuildTPlan make_plan_translated(int R, int Q, int N_B) {
+  BuildTPlan t{};
+  t.base = make_plan(R, N_B);
+  const size_t rr = (size_t)R * R * sizeof(double);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  // the partial sums take two slices' worth per slice (the two sums kept apart)
+  const size_t extra = up((size_t)t.base.nslices * rr);
+  t.base.off_C += extra;
+  t.base.off_A += extra;
+  t.base.off_V += extra;
+  t.base.total += extra;
+  t.off_Phi = t.base.total;
+  t.off_Psi = t.off_Phi + up(rr);
+  t.off_phi = t.off_Psi + up(rr);
+  t.total = t.off_phi + up((size_t)R * Q * sizeof(double2));
+  return t;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+extern "C" size_t rsvd_build_translated_workspace_bytes(int R, int Q, int N_B) {
+  if (R <= 0 || R > rsvd::kMaxR || Q <= 0 || N_B <= 0) return 0;
+  return rsvd::make_plan_translated(R, Q, N_B).total;
+}
+
+extern "C" int rsvd_build_radial_svd_translated(int R, int Q, const double* k, const double* w, const void* templates,
+                                                int N_B, const double* deltas, const double* weights, int T, int H,
+                                                double* U, double* eig, void* workspace, size_t workspace_bytes,
+                                                void* stream) {
+  using namespace rsvd;
+  int rc = check_grid(R, Q, H);
+  if (rc != RSVD_OK) return rc;
+  if (!k || !w || !templates || !U || !eig || !deltas || N_B <= 0 || T <= 0) return RSVD_EINVAL;
+  if (T > kMaxT) return RSVD_EUNSUPPORTED;
+  if (((uintptr_t)templates & 7u) || ((uintptr_t)U & 7u) || ((uintptr_t)eig & 7u)) return RSVD_EINVAL;
+  const BuildTPlan pl = make_plan_translated(R, Q, N_B);
+  if (!workspace || workspace_bytes < pl.total || ((uintptr_t)workspace & 255u)) return RSVD_EWORKSPACE;
+  MomentParams mp{};
+  mp.R = R;
+  mp.Q = Q;
+  mp.T = T;
+  double psum = 0.0;
+  for (int t = 0; t < T; ++t) {
+    const double pw = weights ? weights[t] : 1.0;
+    if (!(pw >= 0.0) || !isfinite(deltas[2 * t]) || !isfinite(deltas[2 * t + 1])) return RSVD_EINVAL;
+    mp.dx[t] = deltas[2 * t];
+    mp.dy[t] = deltas[2 * t + 1];
+    mp.pt[t] = pw;
+    psum += pw;
+  }
+  if (!(psum > 0.0)) return RSVD_EINVAL;
+  for (int t = 0; t < T; ++t) mp.pt[t] /= psum;
+  ReduceTParams rp{};
+  for (int r = 0; r < R; ++r) {
+    if (!(w[r] >= 0.0)) return RSVD_EINVAL;
+    mp.k[r] = k[r];
+    rp.sw[r] = sqrt(w[r]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  double* partial = reinterpret_cast<double*>(ws + pl.base.off_partial);
+  double* C = reinterpret_cast<double*>(ws + pl.base.off_C);
+  double* A = reinterpret_cast<double*>(ws + pl.base.off_A);
+  double* V = reinterpret_cast<double*>(ws + pl.base.off_V);
+  double* Phi = reinterpret_cast<double*>(ws + pl.off_Phi);
+  double* Psi = reinterpret_cast<double*>(ws + pl.off_Psi);
+  double2* phi = reinterpret_cast<double2*>(ws + pl.off_phi);
+
+  dim3 grid(pl.base.nslices, pl.base.ntiles);
+  kernel_partial<true><<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.base.tiles1d,
+                                                  pl.base.nslices, partial);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  kernel_phi<<<(R * Q + 255) / 256, 256, 0, st>>>(mp, phi);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  const int mt = (R + kMomTile - 1) / kMomTile;
+  kernel_moments<<<mt * mt, kMomTile * kMomTile, 0, st>>>(mp, phi, Phi, Psi);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  rp.partial = partial;
+  rp.Phi = Phi;
+  rp.Psi = Psi;
+  rp.C = C;
+  rp.R = R;
+  rp.nslices = pl.base.nslices;
+  rp.N_B = N_B;
+  kernel_reduce_translated<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
   if ((rc = launch_status()) != RSVD_OK) return rc;
   const size_t need = (size_t)2 * R * R * sizeof(double);
   const int use_smem = need <= 160 * 1024 ? 1 : 0;
