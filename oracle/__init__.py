@@ -19,6 +19,8 @@ from .rsvd_ref import (  # noqa: F401
     compress,
     compress_adjoint,
     fb_coefficients,
+    grouped_principal_vectors,
+    grouped_scores,
     half_spectrum_operand,
     lse_loss,
     lse_grad_compressed,

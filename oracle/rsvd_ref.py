@@ -357,3 +357,36 @@ def translation_moments(k: np.ndarray, deltas: np.ndarray, weights: np.ndarray |
     phi = np.einsum("t,rtq->rq", p, np.exp(-1j * k[:, None, None] * proj[None]))
     Psi = (np.conj(phi) @ phi.T) / Q
     return Phi, Psi
+
+
+# ---------------------------------------------------------------------------
+# Section 3.5: one kernel per CTF. The targets of micrograph g are the
+# templates corrected with that micrograph's CTF; the kernel (eq.
+# image_cost_and_kern), its principal vectors and the compressed targets are
+# built per group, and the images of group g are aligned to the targets of g.
+# ---------------------------------------------------------------------------
+def grouped_principal_vectors(S: np.ndarray, w: np.ndarray, ctf: np.ndarray, H: int):
+    """S [nB, R, Q] templates, ctf [G, R] isotropic CTFs: per group g the
+    principal vectors of the kernel of the targets ctf_g x S. Returns
+    (U [G, R, H], lam [G, R])."""
+    Us, lams = [], []
+    for g in range(ctf.shape[0]):
+        U, lam = principal_vectors(radial_kernel(ctf[g][None, :, None] * S, w), H)
+        Us.append(U)
+        lams.append(lam)
+    return np.stack(Us), np.stack(lams)
+
+
+def grouped_scores(images: np.ndarray, offsets: np.ndarray, S: np.ndarray, ctf: np.ndarray, U: np.ndarray,
+                   w: np.ndarray, k: np.ndarray, deltas: np.ndarray) -> np.ndarray:
+    """Real X [nA, T, nB, Q]: image n of group g against the targets ctf_g x S,
+    both compressed with U_g (eq. image_innerproduct_pm)."""
+    out = []
+    for g in range(ctf.shape[0]):
+        A = images[offsets[g]:offsets[g + 1]]
+        if A.shape[0] == 0:
+            continue
+        a = compress(translate(A, k, deltas), U[g], w)
+        b = compress(ctf[g][None, :, None] * S, U[g], w)
+        out.append(scores_compressed(a, b).real)
+    return np.concatenate(out, axis=0)

@@ -11,9 +11,12 @@ from .inputs import (  # noqa: F401
     Blobs,
     PolarGrid,
     Workload,
+    GroupedWorkload,
     blobs_polar_ft,
+    ctf_curves,
     draw_blobs,
     hermitian_noise,
+    make_grouped_workload,
     make_workload,
     make_workload_torch,
     polar_grid,

@@ -269,3 +269,55 @@ def make_workload_torch(N: int, R: int, Q: int, N_B: int, N_A: int, snr: float |
         images[i:i + chunk] = sig.to(torch.complex64)
     truth = dict(j=j0, m=m0, t=t0)
     return grid, deltas, templates, images, truth
+
+
+def ctf_curves(grid: PolarGrid, G: int, seed: int = 0, amp_contrast: float = 0.1) -> np.ndarray:
+    """Isotropic contrast-transfer functions standing in for G micrographs:
+    ctf_g(k) = -[sqrt(1 - A^2) sin(chi_g(k)) + A cos(chi_g(k))], chi_g(k) = pi D_g (k / K)^2 * 8,
+    defocus-like D_g ~ U(0.5, 1.5), amplitude contrast A. Returns float64 [G, R]."""
+    rng = np.random.default_rng(seed)
+    D = rng.uniform(0.5, 1.5, size=G)
+    chi = math.pi * 8.0 * D[:, None] * (grid.k[None, :] / grid.K) ** 2
+    return -(math.sqrt(1.0 - amp_contrast**2) * np.sin(chi) + amp_contrast * np.cos(chi))
+
+
+@dataclass
+class GroupedWorkload:
+    grid: PolarGrid
+    deltas: np.ndarray
+    templates: np.ndarray  # [N_B, R, Q] before any CTF
+    images: np.ndarray  # [N_A, R, Q], image n carries the CTF of its group
+    ctf: np.ndarray  # [G, R]
+    offsets: np.ndarray  # [G + 1]: images of group g are offsets[g] .. offsets[g+1]-1
+    truth_j: np.ndarray
+    truth_m: np.ndarray
+    truth_t: np.ndarray
+
+
+def make_grouped_workload(N: int, R: int, Q: int, N_B: int, N_A: int, G: int, snr: float | None,
+                          T_side: int = 1, seed: int = 0, spacing_px: float = 1.0) -> GroupedWorkload:
+    """Images in G contiguous groups (as consecutive micrographs); image n of
+    group g = ctf_g x (template j0 rotated by a grid angle and translated),
+    plus noise at the given SNR of that CTF-modulated signal."""
+    rng = np.random.default_rng(seed)
+    grid = polar_grid(N, R, Q)
+    deltas = translation_grid(N, T_side, spacing_px)
+    T = deltas.shape[0]
+    tb = draw_blobs(rng, N_B)
+    templates = blobs_polar_ft(grid, tb)
+    ctf = ctf_curves(grid, G, seed + 1)
+    offsets = np.round(np.linspace(0, N_A, G + 1)).astype(np.int64)
+    group = np.searchsorted(offsets, np.arange(N_A), side="right") - 1
+    j0 = rng.integers(0, N_B, size=N_A)
+    m0 = rng.integers(0, Q, size=N_A)
+    t0 = rng.integers(0, T, size=N_A)
+    ib = Blobs(centres=tb.centres[j0], widths=tb.widths[j0], amps=tb.amps[j0])
+    signal = blobs_polar_ft(grid, ib, rotation=2.0 * math.pi * m0 / Q, shift=-deltas[t0])
+    signal = signal * ctf[group][:, :, None]
+    if snr is None:
+        images = signal
+    else:
+        sig2 = polar_norm2(grid, signal) / (snr * R * Q)
+        images = signal + hermitian_noise(rng, grid, sig2)
+    return GroupedWorkload(grid=grid, deltas=deltas, templates=templates, images=images, ctf=ctf, offsets=offsets,
+                           truth_j=j0, truth_m=m0, truth_t=t0)
