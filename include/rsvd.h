@@ -128,6 +128,24 @@ int rsvd_build_radial_svd_translated(int R, int Q, const double* k, const double
                                      double* U, double* eig, void* workspace, size_t workspace_bytes,
                                      void* stream);
 
+/* One kernel per CTF group (section 3.5: the targets of micrograph g are the
+ * templates corrected with its contrast-transfer function, and the kernel of
+ * eq. image_cost_and_kern is built for each group). For isotropic CTFs,
+ * ctf_g(k_r) multiplies ring r, so C_g = diag(ctf_g) C diag(ctf_g) with C the
+ * kernel of the uncorrected templates (built once, FP64); U_g = principal
+ * vectors of C_g; the corrected targets of group g compress with
+ *   U_targets[g] = diag(ctf_g) U_g  (rsvd_compress of the uncorrected templates),
+ * the images of group g with U[g].
+ *   templates  dev complex64 [N_B][R][Q], uncorrected
+ *   ctf        dev double [G][R]: ctf_g(k_r)
+ *   U          dev double [G][R][H]          eig  dev double [G][R], decreasing per group
+ *   U_targets  dev double [G][R][H] or NULL
+ *   workspace  dev, >= rsvd_build_grouped_workspace_bytes(R, Q, N_B, G) bytes, 256-byte aligned */
+size_t rsvd_build_grouped_workspace_bytes(int R, int Q, int N_B, int G);
+int rsvd_build_radial_svd_grouped(int R, int Q, const double* w, const void* templates, int N_B,
+                                  const double* ctf, int G, int H, double* U, double* U_targets,
+                                  double* eig, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Allocation-free form of rsvd_build_radial_svd (the paper has no
  * counterpart; it is a memory-management variant of the call above).
  * For callers that cannot allocate device memory: code that receives only

@@ -13,10 +13,12 @@ from .api import (  # noqa: F401
     align_best,
     align_best_fine,
     align_best_pairs,
+    align_grouped,
     align_marching,
     align_scores,
     align_scores_fine,
     build_radial_svd,
+    build_radial_svd_grouped,
     build_radial_svd_noalloc,
     build_radial_svd_translated,
     build_workspace_bytes,

@@ -115,6 +115,49 @@ def build_radial_svd_translated(k, w, templates: torch.Tensor, H: int, deltas, w
     return U, eig
 
 
+def build_radial_svd_grouped(w, templates: torch.Tensor, ctf: torch.Tensor, H: int, stream=None):
+    """Per-CTF principal vectors. templates complex64 [N_B, R, Q] (uncorrected),
+    ctf float64 [G, R] on the device. Returns (U [G, R, H] for the images of each
+    group, U_targets [G, R, H] = diag(ctf_g) U_g for the templates, eig [G, R])."""
+    _require_cuda(templates, torch.complex64, "templates")
+    _require_cuda(ctf, torch.float64, "ctf")
+    N_B, R, Q = templates.shape
+    G = ctf.shape[0]
+    wa, wp = _host_f64(w)
+    dev = templates.device
+    U = torch.empty((G, R, H), dtype=torch.float64, device=dev)
+    Ut = torch.empty((G, R, H), dtype=torch.float64, device=dev)
+    eig = torch.empty((G, R), dtype=torch.float64, device=dev)
+    need = int(lib().rsvd_build_grouped_workspace_bytes(R, Q, N_B, G))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    check(lib().rsvd_build_radial_svd_grouped(R, Q, wp, _ptr(templates), N_B, _ptr(ctf), G, H, _ptr(U), _ptr(Ut),
+                                              _ptr(eig), _ptr(ws), ws.numel(), _stream(stream)),
+          "rsvd_build_radial_svd_grouped")
+    return U, Ut, eig
+
+
+def align_grouped(k, w, images: torch.Tensor, offsets, templates: torch.Tensor, U: torch.Tensor,
+                  U_targets: torch.Tensor, deltas=None, precision=FP32, stream=None):
+    """Align the images of each CTF group (rows offsets[g] .. offsets[g+1]-1) to
+    that group's corrected targets: compress both with the group's vectors and
+    run align_best per group. Returns best [N_A, N_B], arg [N_A, N_B]."""
+    N_A = images.shape[0]
+    N_B, R, Q = templates.shape
+    H = U.shape[2]
+    T = 1 if deltas is None else np.asarray(deltas).reshape(-1, 2).shape[0]
+    best = torch.empty((N_A, N_B), dtype=torch.float32, device=images.device)
+    arg = torch.empty((N_A, N_B), dtype=torch.int32, device=images.device)
+    for g in range(U.shape[0]):
+        a0, a1 = int(offsets[g]), int(offsets[g + 1])
+        if a1 <= a0:
+            continue
+        cA = compress(k, w, U[g], images[a0:a1], deltas=deltas, precision=precision, stream=stream)
+        cB = compress(k, w, U_targets[g], templates, precision=precision, stream=stream)
+        align_best(cA, a1 - a0, T, cB, N_B, H, Q, precision=precision, out=(best[a0:a1], arg[a0:a1], None),
+                   stream=stream)
+    return best, arg
+
+
 def compressed_bytes(N: int, T: int, H: int, Q: int, precision=FP32) -> int:
     return int(lib().rsvd_compressed_bytes(N, T, H, Q, _prec(precision)))
 

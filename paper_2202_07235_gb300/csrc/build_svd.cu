@@ -168,6 +168,15 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_eig(const double* __res
                                                               int use_smem, int* status) {
   extern __shared__ __align__(16) double jsm[];
   __shared__ double cs_c[kMaxR / 2 + 1], cs_s[kMaxR / 2 + 1];
+  // batched use (one CTA per matrix): matrix blockIdx.x of consecutive R x R blocks
+  {
+    const size_t b = blockIdx.x;
+    C += b * R * R;
+    A += b * R * R;
+    V += b * R * R;
+    U += b * R * H;
+    eig += b * R;
+  }
   __shared__ int pr_p[kMaxR / 2 + 1], pr_q[kMaxR / 2 + 1];
   __shared__ int rotated;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -192,7 +201,9 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_eig(const double* __res
   __syncthreads();
   // rotate while |a_pq| exceeds both a relative (to sqrt(a_pp a_qq)) and an
   // absolute (to the largest diagonal entry) rounding-level threshold
-  const double abs_floor = 1e-17 * anorm;
+  // below a few ulp of the largest diagonal the off-diagonals are rounding noise of
+  // the rotations themselves (kernels with near-zero rings, e.g. at CTF zeros)
+  const double abs_floor = 1e-15 * anorm;
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) rotated = 0;
@@ -657,4 +668,115 @@ extern "C" int rsvd_build_radial_svd_translated(int R, int Q, const double* k, c
     return RSVD_ECUDA;
   jacobi_eig<<<1, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
   return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// One kernel per CTF (section 3.5: the targets of micrograph g are the
+// templates corrected with its CTF, and the kernel of eq. image_cost_and_kern is
+// built per group). An isotropic CTF multiplies ring r by ctf_g(k_r), so the
+// group kernel is C_g = diag(ctf_g) C diag(ctf_g) with C the kernel of the
+// uncorrected templates, and the CTF-corrected targets compress with
+// diag(ctf_g) U_g. C is built once; the G eigen-decompositions run as one
+// batched Jacobi launch (one CTA per group).
+// ---------------------------------------------------------------------------
+namespace rsvd {
+namespace {
+
+__global__ void kernel_scale_groups(const double* __restrict__ C, const double* __restrict__ ctf, int R, int G,
+                                    double* __restrict__ Cg) {
+  const long long RR = (long long)R * R;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < RR * G; i += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(i / RR);
+    const int rc = (int)(i % RR);
+    const int r = rc / R, c = rc % R;
+    Cg[i] = ctf[(size_t)g * R + r] * ctf[(size_t)g * R + c] * C[rc];
+  }
+}
+
+__global__ void kernel_scale_targets(const double* __restrict__ U, const double* __restrict__ ctf, int R, int H, int G,
+                                     double* __restrict__ Ut) {
+  const long long n = (long long)G * R * H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long gr = i / H;  // g * R + r
+    Ut[i] = ctf[gr] * U[i];
+  }
+}
+
+struct BuildGPlan {
+  BuildPlan base;
+  size_t off_Cg, off_Ag, off_Vg, total;
+};
+
+BuildGPlan make_plan_grouped(int R, int N_B, int G) {
+  BuildGPlan t{};
+  t.base = make_plan(R, N_B);
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t grr = (size_t)G * R * R * sizeof(double);
+  t.off_Cg = t.base.total;
+  t.off_Ag = t.off_Cg + up(grr);
+  t.off_Vg = t.off_Ag + up(grr);
+  t.total = t.off_Vg + up(grr);
+  return t;
+}
+
+}  // namespace
+}  // namespace rsvd
+
+extern "C" size_t rsvd_build_grouped_workspace_bytes(int R, int Q, int N_B, int G) {
+  if (R <= 0 || R > rsvd::kMaxR || Q <= 0 || N_B <= 0 || G <= 0) return 0;
+  return rsvd::make_plan_grouped(R, N_B, G).total;
+}
+
+extern "C" int rsvd_build_radial_svd_grouped(int R, int Q, const double* w, const void* templates, int N_B,
+                                             const double* ctf, int G, int H, double* U, double* U_targets,
+                                             double* eig, void* workspace, size_t workspace_bytes, void* stream) {
+  using namespace rsvd;
+  int rc = check_grid(R, Q, H);
+  if (rc != RSVD_OK) return rc;
+  if (!w || !templates || !ctf || !U || !eig || N_B <= 0 || G <= 0) return RSVD_EINVAL;
+  if (G > 65535) return RSVD_EUNSUPPORTED;
+  if (((uintptr_t)templates & 7u) || ((uintptr_t)U & 7u) || ((uintptr_t)eig & 7u) || ((uintptr_t)ctf & 7u) ||
+      ((uintptr_t)U_targets & 7u))
+    return RSVD_EINVAL;
+  const BuildGPlan pl = make_plan_grouped(R, N_B, G);
+  if (!workspace || workspace_bytes < pl.total || ((uintptr_t)workspace & 255u)) return RSVD_EWORKSPACE;
+  ReduceParams rp{};
+  for (int r = 0; r < R; ++r) {
+    if (!(w[r] >= 0.0)) return RSVD_EINVAL;
+    rp.sw[r] = sqrt(w[r]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  double* partial = reinterpret_cast<double*>(ws + pl.base.off_partial);
+  double* C = reinterpret_cast<double*>(ws + pl.base.off_C);
+  double* Cg = reinterpret_cast<double*>(ws + pl.off_Cg);
+  double* Ag = reinterpret_cast<double*>(ws + pl.off_Ag);
+  double* Vg = reinterpret_cast<double*>(ws + pl.off_Vg);
+
+  dim3 grid(pl.base.nslices, pl.base.ntiles);
+  kernel_partial<false><<<grid, kThreads, 0, st>>>(static_cast<const float2*>(templates), N_B, R, Q, pl.base.tiles1d,
+                                                   pl.base.nslices, partial);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  rp.partial = partial;
+  rp.C = C;
+  rp.R = R;
+  rp.nslices = pl.base.nslices;
+  rp.N_B = N_B;
+  kernel_reduce<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  kernel_scale_groups<<<256, 256, 0, st>>>(C, ctf, R, G, Cg);
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  const size_t need = (size_t)2 * R * R * sizeof(double);
+  const int use_smem = need <= 160 * 1024 ? 1 : 0;
+  const size_t smem = use_smem ? need : 0;
+  if (use_smem &&
+      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RSVD_ECUDA;
+  jacobi_eig<<<G, kJacobiThreads, smem, st>>>(Cg, Ag, Vg, R, H, U, eig, use_smem, status_word());
+  if ((rc = launch_status()) != RSVD_OK) return rc;
+  if (U_targets) {
+    kernel_scale_targets<<<256, 256, 0, st>>>(U, ctf, R, H, G, U_targets);
+    if ((rc = launch_status()) != RSVD_OK) return rc;
+  }
+  return RSVD_OK;
 }
