@@ -314,6 +314,46 @@ int rsvd_align_best_pairs(const void* cA, int N_A, int T, const void* cB, int N_
  *   pairs  dev int32 [N_A * keep][2] -- output, for rsvd_align_best_pairs */
 int rsvd_select_pairs(const float* best, int N_A, int N_B, int keep, int32_t* pairs, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Volume alignment (section 4). A volume is given by its spherical-harmonic
+ * coefficients on R frequency shells: complex64 [N][R][L+1][2L+1], element
+ * [n][r][l][m + L] = A_l^m(k_r) (orthonormal harmonics with the Condon-Shortley
+ * phase; entries with |m| > l are ignored). A rotation tau = (gamma, beta, alpha)
+ * is R_z(alpha) R_y(beta) R_z(gamma) and acts on the coefficients as
+ *   (R_tau A)_l^{m1} = sum_{m2} e^{-i m1 alpha} d^l_{m1 m2}(beta) e^{-i m2 gamma} A_l^{m2}
+ * (section 4.2); X(tau) = <A, R_tau B> = sum_r w_r sum_{l,m} conj(A_l^m(k_r)) (R_tau B)_l^m(k_r).
+ * Limits: L <= 31 (alignment: L <= 24 and the shared-memory bound 2 H_C (L+1)(2L+1) complex
+ * values + the Mp x Mp grid within 227 KB), R <= 256, H_C <= 16, H_D <= 8.
+ *
+ * rsvd_build_volume_svd: radial kernel (eq. Volume_simple_radial_kern, l = 0
+ *   excluded, sqrt(w_r w_r') weights) and degree kernel (eq.
+ *   Volume_simple_degree_kern, rows and columns l = 0 zero), averaged over the
+ *   N_B targets, in FP64; U dev double [R][H_C], eigU [R]; V dev double
+ *   [L+1][H_D], eigV [L+1] (principal vectors by decreasing eigenvalue, largest
+ *   entry positive). w host double [R] (the k^2 dk weights).
+ *   workspace >= rsvd_volume_build_workspace_bytes(R, L), 256-byte aligned.
+ * rsvd_volume_tables: the principal-degree Wigner tables (eq.
+ *   principal_degree_wigner) [v_d^T d]_{m1 m2}(beta_b) = sum_l V[l][d] d^l_{m1 m2}(beta_b),
+ *   tables dev float [n_beta][H_D][2L+1][2L+1], betas host double [n_beta] (<= 256).
+ * rsvd_compress_volume: principal-volume-shells (section 4.5)
+ *   out[n][h][l][m + L] = sum_r U[r][h] sqrt(w_r) A_l^m(k_r), complex64 [N][H_C][L+1][2L+1].
+ * rsvd_align_volumes: eq. volume_innerproduct_pm Steps 1, 1b, 2 and 3 per
+ *   (volume, target) pair with the 2-D transform zero-padded to Mp x Mp
+ *   (Mp in {16, 32, 64}, Mp >= 2L+1): X at alpha_a = 2 pi a / Mp, gamma_c = 2 pi c / Mp,
+ *   beta_b of the tables; best[n][j] = max X, arg[n][j] = b Mp^2 + a Mp + c of that
+ *   maximum (smallest among equal values). cA, cB from rsvd_compress_volume.
+ * ------------------------------------------------------------------------ */
+size_t rsvd_volume_build_workspace_bytes(int R, int L);
+int rsvd_build_volume_svd(int R, int L, const double* w, const void* targets, int N_B, int HC, int HD,
+                          double* U, double* eigU, double* V, double* eigV, void* workspace,
+                          size_t workspace_bytes, void* stream);
+int rsvd_volume_tables(int L, int HD, const double* V, const double* betas, int n_beta, float* tables,
+                       void* stream);
+int rsvd_compress_volume(int R, int L, const double* w, const double* U, int HC, const void* volumes, int N,
+                         void* out, void* stream);
+int rsvd_align_volumes(const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V, int HD,
+                       const float* tables, int n_beta, int Mp, float* best, int32_t* arg, void* stream);
+
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).
  * Provided so callers can cross-check the fused kernel. */

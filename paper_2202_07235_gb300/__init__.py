@@ -17,13 +17,16 @@ from .api import (  # noqa: F401
     align_marching,
     align_scores,
     align_scores_fine,
+    align_volumes,
     build_radial_svd,
+    build_volume_svd,
     build_radial_svd_grouped,
     build_radial_svd_noalloc,
     build_radial_svd_translated,
     build_workspace_bytes,
     compress,
     compress_backward,
+    compress_volume,
     compressed_bytes,
     lse_align,
     lse_backward,
@@ -31,4 +34,5 @@ from .api import (  # noqa: F401
     pack,
     select_pairs,
     status,
+    volume_tables,
 )

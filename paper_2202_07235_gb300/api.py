@@ -158,6 +158,69 @@ def align_grouped(k, w, images: torch.Tensor, offsets, templates: torch.Tensor, 
     return best, arg
 
 
+def build_volume_svd(w, targets: torch.Tensor, HC: int, HD: int, stream=None):
+    """Radial (U [R, HC]) and degree (V [L+1, HD]) principal vectors of the
+    targets complex64 [N_B, R, L+1, 2L+1]; returns (U, eigU, V, eigV)."""
+    _require_cuda(targets, torch.complex64, "targets")
+    N_B, R, L1, M = targets.shape
+    L = L1 - 1
+    wa, wp = _host_f64(w)
+    dev = targets.device
+    U = torch.empty((R, HC), dtype=torch.float64, device=dev)
+    eU = torch.empty((R,), dtype=torch.float64, device=dev)
+    V = torch.empty((L1, HD), dtype=torch.float64, device=dev)
+    eV = torch.empty((L1,), dtype=torch.float64, device=dev)
+    need = int(lib().rsvd_volume_build_workspace_bytes(R, L))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    check(lib().rsvd_build_volume_svd(R, L, wp, _ptr(targets), N_B, HC, HD, _ptr(U), _ptr(eU), _ptr(V), _ptr(eV),
+                                      _ptr(ws), ws.numel(), _stream(stream)), "rsvd_build_volume_svd")
+    return U, eU, V, eV
+
+
+def volume_tables(V: torch.Tensor, betas, stream=None) -> torch.Tensor:
+    """[v_d^T d](beta_b) tables, float32 [n_beta, HD, 2L+1, 2L+1]."""
+    _require_cuda(V, torch.float64, "V")
+    L1, HD = V.shape
+    ba, bp = _host_f64(betas)
+    M = 2 * L1 - 1
+    T = torch.empty((ba.size, HD, M, M), dtype=torch.float32, device=V.device)
+    check(lib().rsvd_volume_tables(L1 - 1, HD, _ptr(V), bp, ba.size, _ptr(T), _stream(stream)), "rsvd_volume_tables")
+    return T
+
+
+def compress_volume(w, U: torch.Tensor, volumes: torch.Tensor, stream=None) -> torch.Tensor:
+    """Principal-volume-shells, complex64 [N, HC, L+1, 2L+1]."""
+    _require_cuda(volumes, torch.complex64, "volumes")
+    _require_cuda(U, torch.float64, "U")
+    N, R, L1, M = volumes.shape
+    HC = U.shape[1]
+    wa, wp = _host_f64(w)
+    out = torch.empty((N, HC, L1, M), dtype=torch.complex64, device=volumes.device)
+    check(lib().rsvd_compress_volume(R, L1 - 1, wp, _ptr(U), HC, _ptr(volumes), N, _ptr(out), _stream(stream)),
+          "rsvd_compress_volume")
+    return out
+
+
+def align_volumes(cA: torch.Tensor, cB: torch.Tensor, V: torch.Tensor, tables: torch.Tensor, Mp: int, out=None,
+                  stream=None):
+    """best float32 [N_A, N_B], arg int32 (b*Mp^2 + a*Mp + c)."""
+    _require_cuda(cA, torch.complex64, "cA")
+    _require_cuda(cB, torch.complex64, "cB")
+    _require_cuda(V, torch.float64, "V")
+    _require_cuda(tables, torch.float32, "tables")
+    N_A, HC, L1, _ = cA.shape
+    N_B = cB.shape[0]
+    n_beta, HD = tables.shape[0], tables.shape[1]
+    if out is None:
+        best = torch.empty((N_A, N_B), dtype=torch.float32, device=cA.device)
+        arg = torch.empty((N_A, N_B), dtype=torch.int32, device=cA.device)
+    else:
+        best, arg = out
+    check(lib().rsvd_align_volumes(_ptr(cA), N_A, _ptr(cB), N_B, HC, L1 - 1, _ptr(V), HD, _ptr(tables), n_beta, Mp,
+                                   _ptr(best), _ptr(arg), _stream(stream)), "rsvd_align_volumes")
+    return best, arg
+
+
 def compressed_bytes(N: int, T: int, H: int, Q: int, precision=FP32) -> int:
     return int(lib().rsvd_compressed_bytes(N, T, H, Q, _prec(precision)))
 

@@ -780,3 +780,21 @@ extern "C" int rsvd_build_radial_svd_grouped(int R, int Q, const double* w, cons
   }
   return RSVD_OK;
 }
+
+namespace rsvd {
+
+// Jacobi eigen-solver of `batch` consecutive R x R symmetric matrices (one CTA
+// each): U [batch][R][H] leading vectors, eig [batch][R] decreasing.
+RSVD_HIDDEN int launch_jacobi(const double* C, double* A, double* V, int R, int H, double* U, double* eig, int batch,
+                              cudaStream_t st) {
+  const size_t need = (size_t)2 * R * R * sizeof(double);
+  const int use_smem = need <= 160 * 1024 ? 1 : 0;
+  const size_t smem = use_smem ? need : 0;
+  if (use_smem &&
+      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return RSVD_ECUDA;
+  jacobi_eig<<<batch, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
+  return launch_status();
+}
+
+}  // namespace rsvd
