@@ -322,8 +322,9 @@ int rsvd_select_pairs(const float* best, int N_A, int N_B, int keep, int32_t* pa
  * is R_z(alpha) R_y(beta) R_z(gamma) and acts on the coefficients as
  *   (R_tau A)_l^{m1} = sum_{m2} e^{-i m1 alpha} d^l_{m1 m2}(beta) e^{-i m2 gamma} A_l^{m2}
  * (section 4.2); X(tau) = <A, R_tau B> = sum_r w_r sum_{l,m} conj(A_l^m(k_r)) (R_tau B)_l^m(k_r).
- * Limits: L <= 31 (alignment: L <= 24 and the shared-memory bound 2 H_C (L+1)(2L+1) complex
- * values + the Mp x Mp grid within 227 KB), R <= 256, H_C <= 16, H_D <= 8.
+ * Limits: L <= 31, R <= 256, H_C <= 16, H_D <= 8; alignment also needs the compressed pair,
+ * 2 H_C (L+1)(2L+1) complex64 values, in 227 KB of shared memory (e.g. H_C <= 11 at L = 24,
+ * H_C <= 8 at L = 28).
  *
  * rsvd_build_volume_svd: radial kernel (eq. Volume_simple_radial_kern, l = 0
  *   excluded, sqrt(w_r w_r') weights) and degree kernel (eq.
@@ -334,7 +335,8 @@ int rsvd_select_pairs(const float* best, int N_A, int N_B, int keep, int32_t* pa
  *   workspace >= rsvd_volume_build_workspace_bytes(R, L), 256-byte aligned.
  * rsvd_volume_tables: the principal-degree Wigner tables (eq.
  *   principal_degree_wigner) [v_d^T d]_{m1 m2}(beta_b) = sum_l V[l][d] d^l_{m1 m2}(beta_b),
- *   tables dev float [n_beta][H_D][2L+1][2L+1], betas host double [n_beta] (<= 256).
+ *   tables dev float [n_beta][2L+1][2L+1][8] (element [b][m1+L][m2+L][d], zero for
+ *   d >= H_D), 16-byte aligned; betas host double [n_beta] (<= 256).
  * rsvd_compress_volume: principal-volume-shells (section 4.5)
  *   out[n][h][l][m + L] = sum_r U[r][h] sqrt(w_r) A_l^m(k_r), complex64 [N][H_C][L+1][2L+1].
  * rsvd_align_volumes: eq. volume_innerproduct_pm Steps 1, 1b, 2 and 3 per

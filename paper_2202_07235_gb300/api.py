@@ -177,25 +177,35 @@ def build_volume_svd(w, targets: torch.Tensor, HC: int, HD: int, stream=None):
     return U, eU, V, eV
 
 
+VOL_TABLE_D = 8  # innermost (degree-vector) extent of the Wigner tables
+
+
 def volume_tables(V: torch.Tensor, betas, stream=None) -> torch.Tensor:
-    """[v_d^T d](beta_b) tables, float32 [n_beta, HD, 2L+1, 2L+1]."""
+    """[v_d^T d](beta_b) tables, float32 [n_beta, 2L+1, 2L+1, 8] (element
+    [b, m1+L, m2+L, d], zero for d >= HD)."""
     _require_cuda(V, torch.float64, "V")
     L1, HD = V.shape
     ba, bp = _host_f64(betas)
     M = 2 * L1 - 1
-    T = torch.empty((ba.size, HD, M, M), dtype=torch.float32, device=V.device)
+    T = torch.empty((ba.size, M, M, VOL_TABLE_D), dtype=torch.float32, device=V.device)
     check(lib().rsvd_volume_tables(L1 - 1, HD, _ptr(V), bp, ba.size, _ptr(T), _stream(stream)), "rsvd_volume_tables")
     return T
 
 
-def compress_volume(w, U: torch.Tensor, volumes: torch.Tensor, stream=None) -> torch.Tensor:
+def compress_volume(w, U: torch.Tensor, volumes: torch.Tensor, out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
     """Principal-volume-shells, complex64 [N, HC, L+1, 2L+1]."""
     _require_cuda(volumes, torch.complex64, "volumes")
     _require_cuda(U, torch.float64, "U")
     N, R, L1, M = volumes.shape
     HC = U.shape[1]
     wa, wp = _host_f64(w)
-    out = torch.empty((N, HC, L1, M), dtype=torch.complex64, device=volumes.device)
+    if out is None:
+        out = torch.empty((N, HC, L1, M), dtype=torch.complex64, device=volumes.device)
+    elif tuple(out.shape) != (N, HC, L1, M):
+        raise ValueError("out must be [N, HC, L+1, 2L+1]")
+    else:
+        _require_cuda(out, torch.complex64, "out")
     check(lib().rsvd_compress_volume(R, L1 - 1, wp, _ptr(U), HC, _ptr(volumes), N, _ptr(out), _stream(stream)),
           "rsvd_compress_volume")
     return out
@@ -210,7 +220,7 @@ def align_volumes(cA: torch.Tensor, cB: torch.Tensor, V: torch.Tensor, tables: t
     _require_cuda(tables, torch.float32, "tables")
     N_A, HC, L1, _ = cA.shape
     N_B = cB.shape[0]
-    n_beta, HD = tables.shape[0], tables.shape[1]
+    n_beta, HD = tables.shape[0], V.shape[1]
     if out is None:
         best = torch.empty((N_A, N_B), dtype=torch.float32, device=cA.device)
         arg = torch.empty((N_A, N_B), dtype=torch.int32, device=cA.device)

@@ -180,3 +180,11 @@ def make_volume_workload(N: int, R: int, L: int, N_B: int, N_A: int, snr: float 
         volumes = signal + real_sh_noise(rng, N_A, R, L, sigma2)
     return VolumeWorkload(grid=grid, targets=targets, volumes=volumes, betas=betas, Mp=Mp, truth_j=j0,
                           truth_a=a0, truth_b=b0, truth_c=c0)
+
+
+# Volume-alignment throughput workload: shells of a 48^3 grid (K = 24 pi),
+# R = 24 shells, degrees L = 24 (M = 49 orders), ranks H_C = H_D = 8,
+# M = 49 interior angles, the (alpha, gamma) grid zero-padded to 64 x 64.
+# 96 seeded blob volumes (noisy rotated copies of one target, the shape of a
+# 96-volumes-vs-one-target comparison) are tiled to 96 per SM of a 152-SM GPU.
+VOLUME_CONFIG = dict(N=48, R=24, L=24, HC=8, HD=8, n_beta=49, Mp=64, N_B=1, n_distinct=96, N_A=96 * 152, snr=0.1)

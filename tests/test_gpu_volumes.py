@@ -56,12 +56,15 @@ def test_volume_tables_match_wigner_d():
     T = P.volume_tables(torch.from_numpy(Vm).to(DEV), betas).cpu().numpy()
     P.status()
     M = 2 * L + 1
+    assert T.shape == (len(betas), M, M, 8)
+    assert np.all(T[..., HD:] == 0)
     for b, beta in enumerate(betas):
         ref = np.zeros((HD, M, M))
         for l in range(L + 1):
             s = slice(L - l, L + l + 1)
             ref[:, s, s] += Vm[l][:, None, None] * V.wigner_d(l, beta)[None]
-        assert np.max(np.abs(T[b] - ref)) <= 2e-6 * max(1.0, np.abs(ref).max())
+        got = np.moveaxis(T[b, :, :, :HD], -1, 0)
+        assert np.max(np.abs(got - ref)) <= 2e-6 * max(1.0, np.abs(ref).max())
 
 
 def test_compress_volume_matches_oracle():
@@ -78,7 +81,9 @@ def test_compress_volume_matches_oracle():
 
 
 @pytest.mark.parametrize("L,R,HC,HD,n_beta,Mp,N_A,N_B", [(8, 8, 5, 6, 9, 32, 5, 3), (12, 10, 8, 8, 7, 32, 3, 2),
-                                                          (24, 12, 8, 8, 5, 64, 2, 2), (7, 6, 6, 8, 6, 16, 4, 2)])
+                                                          (24, 12, 8, 8, 5, 64, 2, 2), (7, 6, 6, 8, 6, 16, 4, 2),
+                                                          (10, 8, 6, 6, 5, 64, 3, 2), (20, 10, 7, 5, 4, 64, 2, 1),
+                                                          (28, 12, 6, 8, 4, 64, 2, 1)])
 def test_align_volumes_matches_oracle(L, R, HC, HD, n_beta, Mp, N_A, N_B):
     wl, A, B = _wl(L=L, R=R, N_B=N_B, N_A=N_A, n_beta=n_beta, Mp=Mp, seed=L + Mp)
     g = wl.grid
@@ -127,14 +132,14 @@ def test_volume_limits_are_refused():
     M = 2 * L + 1
     c = torch.zeros((1, HC, L + 1, M), dtype=torch.complex64, device=DEV)
     Vd = torch.zeros((L + 1, HD), dtype=torch.float64, device=DEV)
-    T = torch.zeros((2, HD, M, M), dtype=torch.float32, device=DEV)
+    T = torch.zeros((2, M, M, 8), dtype=torch.float32, device=DEV)
     with pytest.raises(P.RSVDError):  # Mp below 2L + 1
         P.align_volumes(c, c, Vd, T, 16)
     with pytest.raises(P.RSVDError):  # Mp not a supported power of two
         P.align_volumes(c, c, Vd, T, 24)
-    L2 = 25  # (2L+1)^2 above 5 values per thread
-    c2 = torch.zeros((1, 2, L2 + 1, 2 * L2 + 1), dtype=torch.complex64, device=DEV)
-    T2 = torch.zeros((1, HD, 2 * L2 + 1, 2 * L2 + 1), dtype=torch.float32, device=DEV)
+    L2 = 31  # the compressed pair (2 x 8 x 32 x 63 complex values) exceeds shared memory
+    c2 = torch.zeros((1, 8, L2 + 1, 2 * L2 + 1), dtype=torch.complex64, device=DEV)
+    T2 = torch.zeros((1, 2 * L2 + 1, 2 * L2 + 1, 8), dtype=torch.float32, device=DEV)
     with pytest.raises(P.RSVDError):
         P.align_volumes(c2, c2, torch.zeros((L2 + 1, HD), dtype=torch.float64, device=DEV), T2, 64)
     with pytest.raises(P.RSVDError):  # H_D above the limit
