@@ -769,7 +769,8 @@ def run_volumes(args):
                    "l2": "inputs larger than L2 (volumes %.2f GB/GPU), no flush" % (vols.numel() * 8 / 1e9),
                    "precompute_ms": round(precompute_ms, 3)},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2), "peak": round(peak, 2),
-                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": _load_traffic(kname + "@volumes") if args.n_images == 0 else None,
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
                      "align_ms": round(align_ms, 3), "compress_ms": round(comp_ms, 3),
                      "flops_per_pair": _vol_flops_per_pair(L, HC, HD, nb, Mp)},

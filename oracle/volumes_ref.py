@@ -81,7 +81,7 @@ def volume_scores_fft(A: np.ndarray, B: np.ndarray, w: np.ndarray, betas: np.nda
 
 
 # ---------------------------------------------------------------------------
-# Sections 4.5-4.7: radial and degree principal vectors, and the compressed
+# Sections 4.5-4.9: radial and degree principal vectors, and the compressed
 # Steps 1, 1b, 2, 3 (eq. volume_innerproduct_pm).
 # ---------------------------------------------------------------------------
 def volume_radial_kernel(B: np.ndarray, w: np.ndarray) -> np.ndarray:
