@@ -160,36 +160,40 @@ struct VolCompressParams {
   double sw[kMaxR];
 };
 
-__global__ void vol_compress_kernel(const __grid_constant__ VolCompressParams p) {
-  __shared__ float uw_s[kMaxR * kVolMaxHC];  // U[r][h] sqrt(w_r)
-  for (int i = threadIdx.x; i < p.R * kVolMaxHC; i += blockDim.x) {
-    const int r = i / kVolMaxHC, h = i % kVolMaxHC;
+// thread per (volume, l, m): HCT >= HC accumulators (HC rounded up to 4)
+template <int HCT>
+__global__ void __launch_bounds__(256) vol_compress_kernel(const __grid_constant__ VolCompressParams p) {
+  __shared__ float uw_s[kMaxR * HCT];  // U[r][h] sqrt(w_r)
+  for (int i = threadIdx.x; i < p.R * HCT; i += blockDim.x) {
+    const int r = i / HCT, h = i % HCT;
     uw_s[i] = (h < p.HC) ? (float)(p.U[r * p.HC + h] * p.sw[r]) : 0.f;
   }
   __syncthreads();
-  const float* uw = uw_s;
   const int M = 2 * p.L + 1, LM = (p.L + 1) * M;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= (long long)p.N * LM) return;
   const int n = (int)(i / LM), lm = (int)(i % LM);
   const int l = lm / M, m = lm % M - p.L;
-  float2 acc[kVolMaxHC];
+  float2 acc[HCT];
 #pragma unroll
-  for (int h = 0; h < kVolMaxHC; ++h) acc[h] = make_float2(0.f, 0.f);
+  for (int h = 0; h < HCT; ++h) acc[h] = make_float2(0.f, 0.f);
   if (abs(m) <= l) {
+    const float2* a = p.A + (size_t)n * p.R * LM + lm;
+#pragma unroll 4
     for (int r = 0; r < p.R; ++r) {
-      const float2 a = p.A[((size_t)n * p.R + r) * LM + lm];
+      const float2 x = __ldcs(a + (size_t)r * LM);  // streamed once
+      const float* u = uw_s + r * HCT;
 #pragma unroll
-      for (int h = 0; h < kVolMaxHC; ++h) {
-        const float u = uw[r * kVolMaxHC + h];
-        acc[h].x = fmaf(u, a.x, acc[h].x);
-        acc[h].y = fmaf(u, a.y, acc[h].y);
+      for (int h = 0; h < HCT; ++h) {
+        acc[h].x = fmaf(u[h], x.x, acc[h].x);
+        acc[h].y = fmaf(u[h], x.y, acc[h].y);
       }
     }
   }
+  float2* out = p.out + (size_t)n * p.HC * LM + lm;
 #pragma unroll
-  for (int h = 0; h < kVolMaxHC; ++h)
-    if (h < p.HC) p.out[((size_t)n * p.HC + h) * LM + lm] = acc[h];
+  for (int h = 0; h < HCT; ++h)
+    if (h < p.HC) out[(size_t)h * LM] = acc[h];
 }
 
 struct VolAlignParams {
@@ -672,7 +676,16 @@ extern "C" int rsvd_compress_volume(int R, int L, const double* w, const double*
   }
   const long long total = (long long)N * (L + 1) * (2 * L + 1);
   if ((total + 255) / 256 > 0x7fffffffLL) return RSVD_EUNSUPPORTED;
-  vol_compress_kernel<<<(unsigned)((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(cp);
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (HC <= 4)
+    vol_compress_kernel<4><<<grid, 256, 0, st>>>(cp);
+  else if (HC <= 8)
+    vol_compress_kernel<8><<<grid, 256, 0, st>>>(cp);
+  else if (HC <= 12)
+    vol_compress_kernel<12><<<grid, 256, 0, st>>>(cp);
+  else
+    vol_compress_kernel<16><<<grid, 256, 0, st>>>(cp);
   return launch_status();
 }
 

@@ -67,11 +67,12 @@ def test_volume_tables_match_wigner_d():
         assert np.max(np.abs(got - ref)) <= 2e-6 * max(1.0, np.abs(ref).max())
 
 
-def test_compress_volume_matches_oracle():
-    wl, A, B = _wl(L=12, R=10, N_A=4, seed=3)
+@pytest.mark.parametrize("HC", [3, 7, 13])
+def test_compress_volume_matches_oracle(HC):
+    wl, A, B = _wl(L=12, R=14, N_A=4, seed=3)
     g = wl.grid
     rng = np.random.default_rng(2)
-    U = np.linalg.qr(rng.standard_normal((g.R, g.R)))[0][:, :7]
+    U = np.linalg.qr(rng.standard_normal((g.R, g.R)))[0][:, :HC]
     got = P.compress_volume(g.w, torch.from_numpy(U).to(DEV), torch.from_numpy(A).to(DEV)).cpu().numpy()
     P.status()
     ref = V.compress_volume(A.astype(np.complex128), U, g.w)
