@@ -356,6 +356,31 @@ int rsvd_compress_volume(int R, int L, const double* w, const double* U, int HC,
 int rsvd_align_volumes(const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V, int HD,
                        const float* tables, int n_beta, int Mp, float* best, int32_t* arg, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Host-input pipeline: rsvd_compress (templates, then images) and
+ * rsvd_align_best over images and templates held in host memory (pinned for
+ * the copies to overlap), with results written to host memory.
+ *   images     host complex64 [N_A][R][Q], templates host complex64 [N_B][R][Q]
+ *              (polar samples as for rsvd_compress; only psi < Q/2 of each
+ *              ring is copied, the samples the compression reads);
+ *   best, arg  host [N_A][N_B] (lse host [N_A][N_B] or NULL): as rsvd_align_best;
+ *   chunk      images per pipeline stage (e.g. a multiple of 2 x the SM count);
+ *   workspace  device, >= rsvd_align_host_workspace_bytes(R, Q, H, T, N_B,
+ *              chunk, precision, lse != NULL), 256-byte aligned, caller-owned;
+ *   stream     runs the kernels; copy_stream (a different stream) runs the
+ *              copies: the copy of chunk c + 1 overlaps the work on chunk c.
+ * Returns after enqueueing; `stream` waits for the last copy back, so
+ * synchronising `stream` makes every result visible on the host. The host
+ * buffers must stay valid until then. Same limits and precisions as
+ * rsvd_compress and rsvd_align_best.
+ * ------------------------------------------------------------------------ */
+size_t rsvd_align_host_workspace_bytes(int R, int Q, int H, int T, int N_B, int chunk, int precision,
+                                       int want_lse);
+int rsvd_align_best_host(int R, int Q, const double* k, const double* w, const double* U, int H,
+                         const void* images, int N_A, const double* deltas, int T, const void* templates,
+                         int N_B, int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
+                         int chunk, void* workspace, size_t workspace_bytes, void* stream, void* copy_stream);
+
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).
  * Provided so callers can cross-check the fused kernel. */

@@ -12,6 +12,8 @@ from .api import (  # noqa: F401
     LSEAlign,
     align_best,
     align_best_fine,
+    align_best_host,
+    align_host_workspace_bytes,
     align_best_pairs,
     align_grouped,
     align_marching,

@@ -51,6 +51,10 @@ SIGNATURES = {
     "rsvd_align_best_pairs": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
                                       c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
     "rsvd_select_pairs": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "rsvd_align_host_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
+    "rsvd_align_best_host": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_void_p, c_int,
+                                     c_double_p, c_int, c_void_p, c_int, c_int, c_float, c_void_p, c_void_p,
+                                     c_void_p, c_int, c_void_p, c_size_t, c_void_p, c_void_p]),
     "rsvd_volume_build_workspace_bytes": (c_size_t, [c_int, c_int]),
     "rsvd_build_volume_svd": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -231,6 +231,66 @@ def align_volumes(cA: torch.Tensor, cB: torch.Tensor, V: torch.Tensor, tables: t
     return best, arg
 
 
+def align_host_workspace_bytes(R: int, Q: int, H: int, T: int, N_B: int, chunk: int, precision=FP32,
+                               want_lse: bool = False) -> int:
+    return int(lib().rsvd_align_host_workspace_bytes(R, Q, H, T, N_B, chunk, _prec(precision), int(want_lse)))
+
+
+def _require_host(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def align_best_host(k, w, U: torch.Tensor, images: torch.Tensor, templates: torch.Tensor, deltas=None,
+                    precision=FP32, inv_sigma2: float = 1.0, want_lse: bool = False, chunk: int | None = None,
+                    workspace: torch.Tensor | None = None, out=None, stream=None, copy_stream=None):
+    """rsvd_align_best_host: images complex64 [N_A, R, Q] and templates complex64
+    [N_B, R, Q] in host memory (pinned for overlap); returns host (best, arg, lse)
+    after synchronising `stream`. U float64 [R, H] on the device."""
+    precision = _prec(precision)
+    _require_host(images, torch.complex64, "images")
+    _require_host(templates, torch.complex64, "templates")
+    _require_cuda(U, torch.float64, "U")
+    N_A, R, Q = images.shape
+    N_B = templates.shape[0]
+    H = U.shape[1]
+    ka, kp = _host_f64(k)
+    wa, wp = _host_f64(w)
+    if deltas is None:
+        T, dp, da = 1, None, None
+    else:
+        da, dp = _host_f64(deltas)
+        T = da.reshape(-1, 2).shape[0]
+    if chunk is None:
+        sms = torch.cuda.get_device_properties(U.device).multi_processor_count
+        chunk = 8 * sms
+    chunk = max(1, min(int(chunk), N_A))
+    need = align_host_workspace_bytes(R, Q, H, T, N_B, chunk, precision, want_lse)
+    if need == 0:
+        raise ValueError("unsupported sizes for the host pipeline")
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=U.device)
+    if out is None:
+        best = torch.empty((N_A, N_B), dtype=torch.float32).pin_memory()
+        arg = torch.empty((N_A, N_B), dtype=torch.int32).pin_memory()
+        lse = torch.empty((N_A, N_B), dtype=torch.float32).pin_memory() if want_lse else None
+    else:
+        best, arg, lse = out
+    s = stream if stream is not None else torch.cuda.current_stream()
+    cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=U.device)
+    check(lib().rsvd_align_best_host(R, Q, kp, wp, _ptr(U), H, _ptr(images), N_A, dp, T, _ptr(templates), N_B,
+                                     precision, float(inv_sigma2), _ptr(best), _ptr(arg),
+                                     _ptr(lse) if lse is not None else None, chunk, _ptr(workspace),
+                                     workspace.numel(), int(s.cuda_stream), int(cs.cuda_stream)),
+          "rsvd_align_best_host")
+    s.synchronize()
+    return best, arg, lse
+
+
 def compressed_bytes(N: int, T: int, H: int, Q: int, precision=FP32) -> int:
     return int(lib().rsvd_compressed_bytes(N, T, H, Q, _prec(precision)))
 

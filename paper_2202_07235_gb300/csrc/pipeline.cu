@@ -1,0 +1,143 @@
+// Host-input alignment pipeline: images and templates in (pinned) host memory,
+// best/arg (and log-sum-exp) back to host memory, with the host-to-device
+// copies of one chunk of images overlapping the compression and alignment of
+// the previous chunk. Only the half ring psi < pi of each polar sample array is
+// copied: the compression reads no other samples (real images,
+// A(k, psi + pi) = conj A(k, psi)).
+//
+// Streams: `stream` runs compression and alignment, `copy_stream` every copy.
+// Chunk c uses polar buffer c mod 2 and output buffer c mod 2; events order
+//   H2D(c) -> compress(c)          (input ready)
+//   compress(c) -> H2D(c + 2)      (polar buffer free)
+//   align(c) -> D2H(c)             (results ready)
+//   D2H(c) -> align(c + 2)         (output buffer free).
+// On the copy stream H2D(c + 1) is enqueued before D2H(c), so it runs while
+// chunk c is aligned. At return, `stream` waits for the last copy, so
+// synchronising `stream` makes every result visible on the host.
+#include "operand.cuh"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct PipeLayout {
+  size_t polar, tpolar, cA, cB, best, arg, lse, total;
+};
+
+PipeLayout pipe_layout(int R, int Q, int H, int T, int N_B, int chunk, int precision, bool want_lse) {
+  PipeLayout L{};
+  const size_t ring = (size_t)R * Q * sizeof(float2);
+  L.polar = up((size_t)chunk * ring);
+  L.tpolar = up((size_t)N_B * ring);
+  L.cA = up(rsvd_compressed_bytes(chunk, T, H, Q, precision));
+  L.cB = up(rsvd_compressed_bytes(N_B, 1, H, Q, precision));
+  const size_t outs = (size_t)chunk * N_B;
+  L.best = up(outs * sizeof(float));
+  L.arg = up(outs * sizeof(int32_t));
+  L.lse = want_lse ? up(outs * sizeof(float)) : 0;
+  L.total = 2 * L.polar + L.tpolar + L.cA + L.cB + 2 * (L.best + L.arg + L.lse);
+  return L;
+}
+
+struct Events {
+  cudaEvent_t ev[8] = {};
+  int n = 0;
+  bool make() {
+    for (n = 0; n < 8; ++n)
+      if (cudaEventCreateWithFlags(&ev[n], cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+  }
+  ~Events() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+  }
+};
+
+}  // namespace
+
+extern "C" size_t rsvd_align_host_workspace_bytes(int R, int Q, int H, int T, int N_B, int chunk, int precision,
+                                                  int want_lse) {
+  if (R <= 0 || Q <= 0 || H <= 0 || T <= 0 || N_B <= 0 || chunk <= 0) return 0;
+  if (rsvd_compressed_bytes(chunk, T, H, Q, precision) == 0) return 0;
+  return pipe_layout(R, Q, H, T, N_B, chunk, precision, want_lse != 0).total;
+}
+
+extern "C" int rsvd_align_best_host(int R, int Q, const double* k, const double* w, const double* U, int H,
+                                    const void* images, int N_A, const double* deltas, int T,
+                                    const void* templates, int N_B, int precision, float inv_sigma2,
+                                    float* best, int32_t* arg, float* lse, int chunk, void* workspace,
+                                    size_t workspace_bytes, void* stream, void* copy_stream) {
+  if (!k || !w || !U || !images || !templates || !best || !arg || R <= 0 || Q <= 0 || H <= 0 || N_A <= 0 ||
+      N_B <= 0 || T <= 0 || chunk <= 0 || (T > 1 && !deltas))
+    return RSVD_EINVAL;
+  if (Q % 2) return RSVD_EUNSUPPORTED;
+  if (stream == copy_stream) return RSVD_EINVAL;  // the overlap needs two streams
+  chunk = chunk < N_A ? chunk : N_A;
+  const bool want_lse = lse != nullptr;
+  const size_t need = rsvd_align_host_workspace_bytes(R, Q, H, T, N_B, chunk, precision, want_lse ? 1 : 0);
+  if (need == 0) return RSVD_EUNSUPPORTED;
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & (kAlign - 1))) return RSVD_EWORKSPACE;
+  const PipeLayout L = pipe_layout(R, Q, H, T, N_B, chunk, precision, want_lse);
+  char* ws = static_cast<char*>(workspace);
+  char* polar[2] = {ws, ws + L.polar};
+  char* tpolar = ws + 2 * L.polar;
+  char* cA = tpolar + L.tpolar;
+  char* cB = cA + L.cA;
+  char* outb = cB + L.cB;
+  float* best_d[2];
+  int32_t* arg_d[2];
+  float* lse_d[2];
+  for (int b = 0; b < 2; ++b) {
+    char* o = outb + b * (L.best + L.arg + L.lse);
+    best_d[b] = reinterpret_cast<float*>(o);
+    arg_d[b] = reinterpret_cast<int32_t*>(o + L.best);
+    lse_d[b] = want_lse ? reinterpret_cast<float*>(o + L.best + L.arg) : nullptr;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream), cp = static_cast<cudaStream_t>(copy_stream);
+  Events E;
+  if (!E.make()) return RSVD_ECUDA;
+  cudaEvent_t ev_in[2] = {E.ev[0], E.ev[1]}, ev_used[2] = {E.ev[2], E.ev[3]};
+  cudaEvent_t ev_done[2] = {E.ev[4], E.ev[5]}, ev_back[2] = {E.ev[6], E.ev[7]};
+  const size_t pitch = (size_t)Q * sizeof(float2), half = pitch / 2;
+  auto h2d = [&](void* dst, const void* src, size_t rings) {  // psi < pi of each ring
+    return cudaMemcpy2DAsync(dst, pitch, src, pitch, half, rings, cudaMemcpyHostToDevice, cp) == cudaSuccess;
+  };
+  const int nchunk = (N_A + chunk - 1) / chunk;
+  // templates: copy (copy stream), compress (compute stream)
+  if (!h2d(tpolar, templates, (size_t)N_B * R)) return RSVD_ECUDA;
+  if (cudaEventRecord(ev_back[1], cp) != cudaSuccess || cudaStreamWaitEvent(st, ev_back[1], 0) != cudaSuccess)
+    return RSVD_ECUDA;
+  int rc = rsvd_compress(R, Q, k, w, U, H, tpolar, N_B, nullptr, 1, precision, cB, stream);
+  if (rc != RSVD_OK) return rc;
+  auto copy_in = [&](int c) -> int {
+    const int b = c & 1, n0 = c * chunk, n = min(chunk, N_A - n0);
+    if (c >= 2 && cudaStreamWaitEvent(cp, ev_used[b], 0) != cudaSuccess) return RSVD_ECUDA;
+    if (!h2d(polar[b], static_cast<const char*>(images) + (size_t)n0 * R * pitch, (size_t)n * R)) return RSVD_ECUDA;
+    return cudaEventRecord(ev_in[b], cp) == cudaSuccess ? RSVD_OK : RSVD_ECUDA;
+  };
+  if ((rc = copy_in(0)) != RSVD_OK) return rc;
+  for (int c = 0; c < nchunk; ++c) {
+    const int b = c & 1, n0 = c * chunk, n = min(chunk, N_A - n0);
+    if (c + 1 < nchunk && (rc = copy_in(c + 1)) != RSVD_OK) return rc;  // overlaps chunk c's work
+    if (cudaStreamWaitEvent(st, ev_in[b], 0) != cudaSuccess) return RSVD_ECUDA;
+    rc = rsvd_compress(R, Q, k, w, U, H, polar[b], n, deltas, T, precision, cA, stream);
+    if (rc != RSVD_OK) return rc;
+    if (cudaEventRecord(ev_used[b], st) != cudaSuccess) return RSVD_ECUDA;
+    if (c >= 2 && cudaStreamWaitEvent(st, ev_back[b], 0) != cudaSuccess) return RSVD_ECUDA;
+    rc = rsvd_align_best(cA, n, T, cB, N_B, H, Q, precision, inv_sigma2, best_d[b], arg_d[b], lse_d[b], stream);
+    if (rc != RSVD_OK) return rc;
+    if (cudaEventRecord(ev_done[b], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev_done[b], 0) != cudaSuccess)
+      return RSVD_ECUDA;
+    const size_t outs = (size_t)n * N_B, o = (size_t)n0 * N_B;
+    if (cudaMemcpyAsync(best + o, best_d[b], outs * sizeof(float), cudaMemcpyDeviceToHost, cp) != cudaSuccess ||
+        cudaMemcpyAsync(arg + o, arg_d[b], outs * sizeof(int32_t), cudaMemcpyDeviceToHost, cp) != cudaSuccess)
+      return RSVD_ECUDA;
+    if (want_lse &&
+        cudaMemcpyAsync(lse + o, lse_d[b], outs * sizeof(float), cudaMemcpyDeviceToHost, cp) != cudaSuccess)
+      return RSVD_ECUDA;
+    if (cudaEventRecord(ev_back[b], cp) != cudaSuccess) return RSVD_ECUDA;
+  }
+  // the caller's stream waits for the last copies back
+  if (cudaStreamWaitEvent(st, ev_back[(nchunk - 1) & 1], 0) != cudaSuccess) return RSVD_ECUDA;
+  return RSVD_OK;
+}
