@@ -580,6 +580,336 @@ def run_gradient(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Rows f1-f3 (finer grid, principal-mode-marching, translation-aware kernel,
+# per-CTF groups): one JSON line each, `--config fine|marching|translated|grouped`
+# ---------------------------------------------------------------------------
+ROW_CONFIGS = ("fine", "marching", "translated", "grouped")
+
+
+def _row_init(**kw):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    _W.update(kw)
+
+
+def _row_oracle(job):
+    """One oracle task of a row's cpu_baseline: (row, images chunk [, group])."""
+    import oracle as O
+
+    row, A = job[0], job[1]
+    if row == "fine":  # compress + finer-grid scores (section 2.4) + max/argmax
+        a_c = O.compress(O.translate(A, _W["k"], _W["deltas"]), _W["U"], _W["w"])
+        return O.align_best(O.scores_fine(a_c, _W["b_c"], _W["P"]))
+    if row == "marching":  # the full pass at the fine rank that marching approximates
+        a_c = O.compress(O.translate(A, _W["k"], _W["deltas"]), _W["U"], _W["w"])
+        return O.align_best(O.scores_compressed(a_c, _W["b_c"]).real)
+    if row == "grouped":  # image chunk of one group against that group's targets
+        g = job[2]
+        a_c = O.compress(O.translate(A, _W["k"], _W["deltas"]), _W["U"][g], _W["w"])
+        return O.align_best(O.scores_compressed(a_c, _W["b_c"][g]).real)
+    raise ValueError(row)
+
+
+def _timed(step, K, W, stream, torch, P):
+    for _ in range(W):
+        step()
+    P.status()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    P.status()
+    return t0.elapsed_time(t1) / K
+
+
+def _pool_run(jobs, init_kw):
+    import multiprocessing as mp
+
+    n = _cores()
+    pool = mp.get_context("spawn").Pool(n, initializer=_row_init_kw, initargs=(init_kw,))
+    try:
+        pool.map(_row_oracle, jobs[:n])  # warm the workers
+        t0 = time.perf_counter()
+        res = pool.map(_row_oracle, jobs)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    return res, wall, n
+
+
+def _row_init_kw(kw):
+    _row_init(**kw)
+
+
+def run_rows(args):
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import paper_2202_07235_gb300 as P
+    from synthetic import CONFIGS, ctf_curves, make_workload_torch
+
+    rank, world, local = _dist_env()
+    row = args.config
+    cfg = dict(CONFIGS["throughput"])
+    defaults = {"fine": 2048, "marching": 8192, "translated": 8192, "grouped": 8192}
+    cfg["N_A"] = args.n_images or defaults[row]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.lib()
+    stream = torch.cuda.current_stream()
+    N_A, N_B, Q, R = cfg["N_A"], cfg["N_B"], cfg["Q"], cfg["R"]
+    grid, deltas, tmpl, _, _ = make_workload_torch(**{**cfg, "N_A": 1}, seed=1000, device=dev)
+    T = deltas.shape[0]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_alu = sms * 128 * 2 * 2.07e9 / 1e12
+    K, W = args.steps, args.warmup
+    want_cpu = not args.no_cpu_baseline and rank == 0
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    out = {"n_gpus": 1, "steps": K, "warmup": W, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)"}
+
+    if row == "translated":
+        # f2: translation-aware kernel C and its principal vectors (section 5), H = 12,
+        # the 9 alignment translations as mu_delta; one step = one build
+        H = cfg["H"]
+        P.build_radial_svd_translated(grid.k, grid.w, tmpl, H, deltas)
+        clocks.start()
+        ms = _timed(lambda: P.build_radial_svd_translated(grid.k, grid.w, tmpl, H, deltas), K, W, stream, torch, P)
+        clk = clocks.stop()
+        U, eig = P.build_radial_svd_translated(grid.k, grid.w, tmpl, H, deltas)
+        # algorithmic FP64 work: the real part of conj(b_r) b_r' for every ring pair, slot and
+        # template (4 flops; Hermitian symmetry not exploited); the Jacobi solve is extra
+        f64 = R * R * (Q // 2) * N_B * 4
+        tf = f64 / (ms / 1e3) / 1e12
+        peak64 = 1.25  # nominal FP64 rate of the part
+        out.update({"metric": "translation-aware kernel builds/sec", "value": 1e3 / ms, "unit": "builds/s",
+                    "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+                    "config": {"workload": f"f2 translation-aware C + principal vectors: {N_B} templates, R={R}, "
+                                           f"Q={Q}, T={T} translations (3x3, 1 px, uniform), H={H}"},
+                    "roofline": {"bound": "alu", "kernel": "kernel_partial<true> + kernel_phi + jacobi_eig",
+                                 "achieved": round(tf, 4), "peak": peak64, "unit": "TFLOP/s (FP64)",
+                                 "frac": round(tf / peak64, 4), "traffic": None,
+                                 "note": "whole build time against the FP64 work of the kernel's Parseval sums; "
+                                         "peak = nominal FP64 rate; the one-CTA Jacobi solve is latency-bound"},
+                    "gpu_launches": None, "clocks": clk})
+        if want_cpu:
+            Bh = tmpl.cpu().numpy().astype(np.complex128)
+            t0 = time.perf_counter()
+            Kf = O.radial_kernel_translated_factored(Bh, grid.w, grid.k, deltas)
+            Uo, lo = O.principal_vectors(Kf, H)
+            wall = time.perf_counter() - t0
+            Ug, eg = U.cpu().numpy(), eig.cpu().numpy()
+            ext = np.r_[np.inf, lo, -np.inf]
+            gap = np.minimum(ext[:H] - ext[1:H + 1], ext[1:H + 1] - ext[2:H + 2])
+            ok = gap > 1e-6 * lo[0]
+            out["cpu_baseline"] = {"value": 1.0 / wall, "unit": "builds/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"the whole build on all {N_B} templates: factorised kernel "
+                                             f"sqrt(w w') Re[S Phi - m Psi] + eigh (FP64 numpy, one process; the "
+                                             f"definition by explicit expectation takes about 0.5 s per template), "
+                                             f"{wall:.1f} s"}
+            out["error"] = {"vs": "FP64 oracle (all templates)",
+                            "eig_max_rel": float(np.max(np.abs(eg - lo)) / abs(lo[0])),
+                            "U_max_abs_separated": float(np.max(np.abs(Ug[:, ok] - Uo[:, ok]))) if ok.any() else None}
+        print(json.dumps(out))
+        return
+
+    _, _, _, imgs, _ = make_workload_torch(**cfg, seed=2000, device=dev)
+    if row == "fine":
+        # f1: X on the P-times finer rotation grid (section 2.4), P = 2, generic pair kernel
+        H, Pf = cfg["H"], 2
+        U, _ = P.build_radial_svd(grid.w, tmpl, H)
+        cB = P.compress(grid.k, grid.w, U, tmpl)
+        cA = torch.empty((N_A * T, H, Q // 2, 2), dtype=torch.float32, device=dev)
+        res = {}
+
+        def step():
+            P.compress(grid.k, grid.w, U, imgs, deltas=deltas, out=cA)
+            res["b"] = P.align_best_fine(cA, N_A, T, cB, N_B, H, Q, Pf)
+
+        clocks.start()
+        ms = _timed(step, K, W, stream, torch, P)
+        clk = clocks.stop()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.align_best_fine(cA, N_A, T, cB, N_B, H, Q, Pf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        align_ms = e0.elapsed_time(e1)
+        pairs = N_A * T * N_B
+        PQ = Pf * Q
+        flops = pairs * (8 * H * (Q // 2 + 1) + 2.5 * PQ * math.log2(PQ) + 2 * PQ)
+        ach = flops / (align_ms / 1e3) / 1e12
+        out.update({"metric": "pair·translation·rotation scores/sec (2x finer rotation grid)",
+                    "value": pairs * PQ / (ms / 1e3), "unit": "scores/s", "ms_per_step": ms,
+                    "higher_is_better": True,
+                    "config": {"workload": "f1 finer grid: " + _workload_desc(cfg) + f", P={Pf} ({PQ} angles)"},
+                    "roofline": {"bound": "alu", "kernel": "pair_kernel (P = 2)", "achieved": round(ach, 2),
+                                 "peak": round(peak_alu, 2), "unit": "TFLOP/s", "frac": round(ach / peak_alu, 4),
+                                 "traffic": None, "align_ms": round(align_ms, 3)},
+                    "gpu_launches": 2, "clocks": clk})
+        best, arg, _ = res["b"]
+        if want_cpu:
+            Un = U.cpu().numpy()
+            b_c = O.compress(tmpl.cpu().numpy().astype(np.complex128), Un, grid.w)
+            n_s = 2 * _cores()
+            A = imgs[:n_s].cpu().numpy().astype(np.complex128)
+            jobs = [("fine", A[i:i + 1]) for i in range(n_s)]
+            r, wall, ncores = _pool_run(jobs, dict(k=grid.k, w=grid.w, deltas=deltas, U=Un, b_c=b_c, P=Pf))
+            rb = np.concatenate([x[0] for x in r])
+            ra = np.concatenate([x[1] for x in r])
+            gb, ga = best[:n_s].cpu().numpy(), arg[:n_s].cpu().numpy()
+            out["cpu_baseline"] = {"value": n_s * T * N_B * PQ / wall, "unit": "scores/s", "cores": ncores,
+                                   "kind": "oracle",
+                                   "sample": f"{n_s} images x {T} x {N_B} templates x {PQ} angles (FP64 numpy "
+                                             f"oracle, direct sum over the fine grid), {wall:.1f} s"}
+            out["error"] = {"vs": "FP64 oracle on the sample", "pairs": int(n_s * N_B),
+                            "best_max_rel": float(np.max(np.abs(gb - rb) / np.maximum(np.abs(rb), 1e-30))),
+                            "argmax_agree": float(np.mean(ga == ra))}
+        print(json.dumps(out))
+        return
+
+    if row == "marching":
+        # f1: principal-mode-marching (section 5): coarse pass at H0 = 8, keep 8 templates
+        # per image, rescore them at H1 = 16; compared with the full pass at H1
+        H0, H1, keep = 8, 16, 8
+        U1, _ = P.build_radial_svd(grid.w, tmpl, H1)
+        U0 = U1[:, :H0].contiguous()
+        cB0 = P.compress(grid.k, grid.w, U0, tmpl)
+        cB1 = P.compress(grid.k, grid.w, U1, tmpl)
+        cA0 = torch.empty((N_A * T, H0, Q // 2, 2), dtype=torch.float32, device=dev)
+        cA1 = torch.empty((N_A * T, H1, Q // 2, 2), dtype=torch.float32, device=dev)
+        res = {}
+
+        def step():
+            P.compress(grid.k, grid.w, U0, imgs, deltas=deltas, out=cA0)
+            P.compress(grid.k, grid.w, U1, imgs, deltas=deltas, out=cA1)
+            res["m"] = P.align_marching((cA0, cB0, H0), (cA1, cB1, H1), N_A, T, N_B, Q, keep)
+
+        def full():
+            P.compress(grid.k, grid.w, U1, imgs, deltas=deltas, out=cA1)
+            res["f"] = P.align_best(cA1, N_A, T, cB1, N_B, H1, Q)
+
+        clocks.start()
+        ms = _timed(step, K, W, stream, torch, P)
+        clk = clocks.stop()
+        ms_full = _timed(full, max(2, K // 2), 2, stream, torch, P)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.align_best(cA0, N_A, T, cB0, N_B, H0, Q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        coarse_ms = e0.elapsed_time(e1)
+        pairs_m, b1, a1, _ = res["m"]
+        bf, af, _ = res["f"]
+        pr = pairs_m.cpu().numpy().reshape(N_A, keep, 2)
+        b1n = b1.cpu().numpy().reshape(N_A, keep)
+        a1n = a1.cpu().numpy().reshape(N_A, keep)
+        sel = np.argmax(b1n, axis=1)
+        j_m = pr[np.arange(N_A), sel, 1]
+        bfn, afn = bf.cpu().numpy(), af.cpu().numpy()
+        j_f = np.argmax(bfn, axis=1)
+        agree_j = float(np.mean(j_m == j_f))
+        agree_arg = float(np.mean((j_m == j_f) & (a1n[np.arange(N_A), sel] == afn[np.arange(N_A), j_f])))
+        pairs = N_A * T * N_B
+        flops = pairs * _alg_flops_per_pair(H0, Q)
+        ach = flops / (coarse_ms / 1e3) / 1e12
+        out.update({"metric": "pair·translation·rotation scores/sec (marching: coarse H=8 pass + rescoring of "
+                              "8 templates per image at H=16)",
+                    "value": pairs * Q / (ms / 1e3), "unit": "scores/s", "ms_per_step": ms, "higher_is_better": True,
+                    "config": {"workload": "f1 principal-mode-marching: " + _workload_desc({**cfg, "H": H1}),
+                               "H0": H0, "H1": H1, "keep": keep, "full_pass_ms": round(ms_full, 3),
+                               "speedup_vs_full_pass": round(ms_full / ms, 3),
+                               "best_template_agrees_with_full_pass": agree_j,
+                               "best_template_and_argmax_agree": agree_arg},
+                    "roofline": {"bound": "alu", "kernel": "ws_align_kernel<128,8> (coarse pass)",
+                                 "achieved": round(ach, 2), "peak": round(peak_alu, 2), "unit": "TFLOP/s",
+                                 "frac": round(ach / peak_alu, 4), "traffic": None, "coarse_ms": round(coarse_ms, 3)},
+                    "gpu_launches": 5, "clocks": clk})
+        if want_cpu:
+            Un = U1.cpu().numpy()
+            b_c = O.compress(tmpl.cpu().numpy().astype(np.complex128), Un, grid.w)
+            n_s = 2 * _cores()
+            A = imgs[:n_s].cpu().numpy().astype(np.complex128)
+            jobs = [("marching", A[i:i + 1]) for i in range(n_s)]
+            r, wall, ncores = _pool_run(jobs, dict(k=grid.k, w=grid.w, deltas=deltas, U=Un, b_c=b_c))
+            rb = np.concatenate([x[0] for x in r])
+            out["cpu_baseline"] = {"value": n_s * T * N_B * Q / wall, "unit": "scores/s", "cores": ncores,
+                                   "kind": "oracle",
+                                   "sample": f"{n_s} images x {T} x {N_B} templates x {Q} angles, full pass at "
+                                             f"H={H1} (FP64 numpy oracle), {wall:.1f} s"}
+            jo = np.argmax(rb, axis=1)
+            out["error"] = {"vs": "FP64 oracle full pass at H=16 on the sample",
+                            "best_template_agrees": float(np.mean(j_m[:n_s] == jo)),
+                            "best_rel": float(np.max(np.abs(b1n[np.arange(n_s), sel[:n_s]] - rb[np.arange(n_s), jo])
+                                                     / np.abs(rb[np.arange(n_s), jo])))}
+        print(json.dumps(out))
+        return
+
+    if row == "grouped":
+        # f3: 17 CTF groups (section 3.5): per group U_g, images of group g against the
+        # targets ctf_g x templates, both compressed with the group's vectors
+        H, G = cfg["H"], 17
+        ctf = ctf_curves(grid, G, seed=1)
+        offsets = np.round(np.linspace(0, N_A, G + 1)).astype(np.int64)
+        for g in range(G):  # image n of group g carries ctf_g
+            imgs[offsets[g]:offsets[g + 1]] *= torch.as_tensor(ctf[g], device=dev)[None, :, None].to(torch.complex64)
+        ctf_d = torch.as_tensor(ctf, device=dev)
+        U, Ut, _ = P.build_radial_svd_grouped(grid.w, tmpl, ctf_d, H)
+        res = {}
+
+        def step():
+            res["b"] = P.align_grouped(grid.k, grid.w, imgs, offsets, tmpl, U, Ut, deltas=deltas)
+
+        clocks.start()
+        ms = _timed(step, K, W, stream, torch, P)
+        clk = clocks.stop()
+        best, arg = res["b"]
+        pairs = N_A * T * N_B
+        out.update({"metric": "pair·translation·rotation scores/sec (17 CTF groups)", "value": pairs * Q / (ms / 1e3),
+                    "unit": "scores/s", "ms_per_step": ms, "higher_is_better": True,
+                    "config": {"workload": "f3 per-CTF groups: " + _workload_desc(cfg) + f", G={G} groups"},
+                    "roofline": {"bound": "alu", "kernel": "ws_align_kernel<128,12> (17 launches)",
+                                 "achieved": round(pairs * _alg_flops_per_pair(H, Q) / (ms / 1e3) / 1e12, 2),
+                                 "peak": round(peak_alu, 2), "unit": "TFLOP/s",
+                                 "frac": round(pairs * _alg_flops_per_pair(H, Q) / (ms / 1e3) / 1e12 / peak_alu, 4),
+                                 "traffic": None, "note": "whole step (compression included) in the achieved figure"},
+                    "gpu_launches": 3 * G, "clocks": clk})
+        if want_cpu:
+            Un, Utn = U.cpu().numpy(), Ut.cpu().numpy()
+            S = tmpl.cpu().numpy().astype(np.complex128)
+            b_c = np.stack([O.compress(ctf[g][None, :, None] * S, Un[g], grid.w) for g in range(G)])
+            ncores = _cores()
+            idx = [int(offsets[g]) for g in range(G)][:ncores] + [int(offsets[g]) + 1 for g in range(G)][:ncores]
+            jobs = []
+            for i in idx:
+                g = int(np.searchsorted(offsets, i, side="right") - 1)
+                jobs.append(("grouped", imgs[i:i + 1].cpu().numpy().astype(np.complex128), g))
+            r, wall, ncores = _pool_run(jobs, dict(k=grid.k, w=grid.w, deltas=deltas, U=Un, b_c=b_c))
+            rb = np.concatenate([x[0] for x in r])
+            ra = np.concatenate([x[1] for x in r])
+            gb, ga = best.cpu().numpy()[idx], arg.cpu().numpy()[idx]
+            out["cpu_baseline"] = {"value": len(idx) * T * N_B * Q / wall, "unit": "scores/s", "cores": ncores,
+                                   "kind": "oracle",
+                                   "sample": f"{len(idx)} images from {min(G, ncores)} groups x {T} x {N_B} targets "
+                                             f"x {Q} angles (FP64 numpy oracle), {wall:.1f} s"}
+            out["error"] = {"vs": "FP64 oracle on the sample", "pairs": int(len(idx) * N_B),
+                            "best_max_rel": float(np.max(np.abs(gb - rb) / np.maximum(np.abs(rb), 1e-30))),
+                            "argmax_agree": float(np.mean(ga == ra))}
+        print(json.dumps(out))
+        return
+
+
 def _vol_oracle_init(w, U, V, betas, Mp, b_c):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     _W.update(w=w, U=U, V=V, betas=betas, Mp=Mp, b_c=b_c)
@@ -961,7 +1291,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference" and args.config == "volumes":
+    if args.impl == "reference" and args.config in ROW_CONFIGS:
+        if _dist_env()[0] == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the FP64 oracle on the "
+                              "throughput and volume workloads; each row line (--config fine|marching|translated|"
+                              "grouped) carries its own oracle timing in cpu_baseline"}))
+    elif args.impl == "reference" and args.config == "volumes":
         run_reference_volumes(args)
     elif args.impl == "reference":
         run_reference(args)
@@ -969,6 +1304,8 @@ def main():
         run_gradient(args)
     elif args.config == "volumes":
         run_volumes(args)
+    elif args.config in ROW_CONFIGS:
+        run_rows(args)
     else:
         run_ours(args)
 

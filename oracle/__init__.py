@@ -39,4 +39,5 @@ from .rsvd_ref import (  # noqa: F401
     scores_fine,
     translate,
     translation_moments,
+    radial_kernel_translated_factored,
 )

@@ -359,6 +359,19 @@ def translation_moments(k: np.ndarray, deltas: np.ndarray, weights: np.ndarray |
     return Phi, Psi
 
 
+def radial_kernel_translated_factored(B: np.ndarray, w: np.ndarray, k: np.ndarray, deltas: np.ndarray,
+                                      weights: np.ndarray | None = None) -> np.ndarray:
+    """The same kernel as radial_kernel_translated in the factorised form
+    K = sqrt(w w') Re[S Phi - m Psi] (section 5): S_{rr'} = mean_j sum_q conj(b_j(r, q)) b_j(r', q)
+    over all q, m_{rr'} = mean_j conj(b_j(r, 0)) b_j(r', 0), with b the FB
+    coefficients and Phi, Psi from translation_moments."""
+    Phi, Psi = translation_moments(k, deltas, weights, B.shape[-1])
+    b = fb_coefficients(B)
+    S = np.einsum("jrq,jsq->rs", np.conj(b), b) / B.shape[0]
+    m = np.einsum("jr,js->rs", np.conj(b[..., 0]), b[..., 0]) / B.shape[0]
+    return np.sqrt(np.outer(w, w)) * (S * Phi - m * Psi).real
+
+
 # ---------------------------------------------------------------------------
 # Section 3.5: one kernel per CTF. The targets of micrograph g are the
 # templates corrected with that micrograph's CTF; the kernel (eq.

@@ -59,11 +59,7 @@ def test_factorised_kernel_equals_the_definition():
     g, B, deltas = _small(nB=3, Q=32, R=10, seed=8)
     weights = np.array([1.0, 2.0, 2.0, 1.0])
     K = O.radial_kernel_translated(B, g.w, g.k, deltas, weights)
-    Phi, Psi = O.translation_moments(g.k, deltas, weights, g.Q)
-    b = O.fb_coefficients(B)  # [nB, R, Q]
-    S = np.einsum("jrq,jsq->rs", np.conj(b), b) / B.shape[0]
-    m = np.einsum("jr,js->rs", np.conj(b[..., 0]), b[..., 0]) / B.shape[0]
-    Kf = np.sqrt(np.outer(g.w, g.w)) * (S * Phi - m * Psi).real
+    Kf = O.radial_kernel_translated_factored(B, g.w, g.k, deltas, weights)
     assert np.allclose(K, Kf, rtol=0, atol=1e-12 * np.abs(K).max())
 
 
