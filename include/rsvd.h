@@ -294,9 +294,22 @@ int rsvd_compress_backward(int R, int Q, const double* k, const double* w, const
  *   pairs, dev int32 [K][2] (8-byte aligned); best, arg, lse dev [K]. A pair
  *   outside [0, N_A) x [0, N_B) leaves its outputs unwritten and records
  *   RSVD_EDEVICE in the status word.
+ * rsvd_align_best_fine_shifted: the result of rsvd_align_best_fine (up to
+ *   rounding) from P passes of rsvd_align_best (the fused kernels): the
+ *   landscape at gamma_m + 2 pi p / (P Q) is the coarse landscape of the
+ *   templates rotated by p/P of a grid step, b_h(q) e^{-i q 2 pi p / (P Q)} for
+ *   0 < |q| < Q/2 with b_h(Q/2) scaled by cos(pi p / P). Passes merge in place
+ *   (ties keep the smaller fine index; lse by log-sum-exp). P in {1, 2, 4, 8},
+ *   Q and H as rsvd_align_best, RSVD_FP32 compressed rings;
+ *   workspace >= rsvd_align_fine_workspace_bytes(N_A, N_B, H, Q, P, lse != NULL),
+ *   256-byte aligned.
  * ------------------------------------------------------------------------ */
 int rsvd_align_scores_fine(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int P,
                            int precision, float* X, void* stream);
+size_t rsvd_align_fine_workspace_bytes(int N_A, int N_B, int H, int Q, int P, int want_lse);
+int rsvd_align_best_fine_shifted(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int P,
+                                 float inv_sigma2, float* best, int32_t* arg, float* lse, void* workspace,
+                                 size_t workspace_bytes, void* stream);
 int rsvd_align_best_fine(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int P,
                          int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
                          void* stream);

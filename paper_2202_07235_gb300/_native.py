@@ -51,6 +51,9 @@ SIGNATURES = {
     "rsvd_align_best_pairs": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
                                       c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
     "rsvd_select_pairs": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "rsvd_align_fine_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
+    "rsvd_align_best_fine_shifted": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float,
+                                             c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rsvd_align_host_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
     "rsvd_align_best_host": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_void_p, c_int,
                                      c_double_p, c_int, c_void_p, c_int, c_int, c_float, c_void_p, c_void_p,

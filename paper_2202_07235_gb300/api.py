@@ -380,15 +380,29 @@ def align_scores_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B:
 
 
 def align_best_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int, P: int,
-                    inv_sigma2: float = 1.0, want_lse: bool = False, stream=None):
-    """best / arg (t*P*Q + m') / lse on the P-times finer rotation grid."""
+                    inv_sigma2: float = 1.0, want_lse: bool = False, method: str = "shifted", workspace=None,
+                    stream=None):
+    """best / arg (t*P*Q + m') / lse on the P-times finer rotation grid.
+    method "shifted": P passes of the fused kernels against templates rotated by
+    p/P of a grid step (rsvd_align_best_fine_shifted); "pair": the generic
+    per-pair kernel with the zero-padded transform (rsvd_align_best_fine)."""
     dev = cA.device
     best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
     arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
     lse = torch.empty((N_A, N_B), dtype=torch.float32, device=dev) if want_lse else None
-    check(lib().rsvd_align_best_fine(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, FP32, float(inv_sigma2), _ptr(best),
-                                     _ptr(arg), _ptr(lse) if lse is not None else None, _stream(stream)),
-          "rsvd_align_best_fine")
+    lp = _ptr(lse) if lse is not None else None
+    if method == "shifted":
+        need = int(lib().rsvd_align_fine_workspace_bytes(N_A, N_B, H, Q, P, int(want_lse)))
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+        check(lib().rsvd_align_best_fine_shifted(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, float(inv_sigma2),
+                                                 _ptr(best), _ptr(arg), lp, _ptr(workspace), workspace.numel(),
+                                                 _stream(stream)), "rsvd_align_best_fine_shifted")
+    elif method == "pair":
+        check(lib().rsvd_align_best_fine(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, FP32, float(inv_sigma2),
+                                         _ptr(best), _ptr(arg), lp, _stream(stream)), "rsvd_align_best_fine")
+    else:
+        raise ValueError(f"unknown method {method}")
     return best, arg, lse
 
 

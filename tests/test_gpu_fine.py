@@ -64,16 +64,29 @@ def test_fine_grid_with_factor_one_is_the_plain_landscape():
     assert torch.equal(X1, X0)
 
 
-@pytest.mark.parametrize("Q,R,H,T_side,Pf", [(128, 32, 8, 2, 4), (256, 64, 12, 3, 2)])
-def test_align_best_fine_matches_oracle(Q, R, H, T_side, Pf):
+@pytest.mark.parametrize("method", ["shifted", "pair"])
+@pytest.mark.parametrize("Q,R,H,T_side,Pf", [(128, 32, 8, 2, 4), (256, 64, 12, 3, 2), (256, 64, 16, 1, 1)])
+def test_align_best_fine_matches_oracle(Q, R, H, T_side, Pf, method):
     wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=6, N_A=9, T_side=T_side, H=H, seed=7 * Pf)
     cA, cB, a, b, T = _compressed(wl, A, B, U)
-    best, arg, lse = P.align_best_fine(cA, 9, T, cB, 6, H, Q, Pf, inv_sigma2=0.5, want_lse=True)
+    best, arg, lse = P.align_best_fine(cA, 9, T, cB, 6, H, Q, Pf, inv_sigma2=0.5, want_lse=True, method=method)
     P.status()
     check_best(O.scores_fine(a, b, Pf), best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 0.5)
 
 
-def test_fine_grid_recovers_off_grid_rotations():
+@pytest.mark.parametrize("Q,R,H,T_side,Pf,N_A,N_B", [(512, 48, 16, 2, 2, 5, 4), (256, 64, 12, 1, 8, 4, 3),
+                                                      (128, 32, 5, 3, 2, 37, 21)])
+def test_shifted_fine_grid_beyond_the_pair_kernel(Q, R, H, T_side, Pf, N_A, N_B):
+    """Shifted passes cover P Q > 1024 and run on the fused kernels (several tiles, ragged)."""
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, seed=Q + Pf)
+    cA, cB, a, b, T = _compressed(wl, A, B, U)
+    best, arg, lse = P.align_best_fine(cA, N_A, T, cB, N_B, H, Q, Pf, want_lse=True)
+    P.status()
+    check_best(O.scores_fine(a, b, Pf), best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
+
+
+@pytest.mark.parametrize("method", ["shifted", "pair"])
+def test_fine_grid_recovers_off_grid_rotations(method):
     """Noiseless images = templates rotated analytically by half-grid angles:
     at P = 2 the argmax lands on the odd fine angle 2 m0 + 1 for every image."""
     from synthetic.inputs import blobs_polar_ft, draw_blobs, polar_grid
@@ -89,7 +102,7 @@ def test_fine_grid_recovers_off_grid_rotations():
     Ut = torch.from_numpy(U).to(DEV)
     cA = P.compress(grid.k, grid.w, Ut, torch.from_numpy(A).to(DEV))
     cB = P.compress(grid.k, grid.w, Ut, torch.from_numpy(B).to(DEV))
-    best, arg, _ = P.align_best_fine(cA, 6, 1, cB, 6, R, Q, Pf)
+    best, arg, _ = P.align_best_fine(cA, 6, 1, cB, 6, R, Q, Pf, method=method)
     P.status()
     arg = arg.cpu().numpy()
     assert np.array_equal(np.diag(arg), 2 * m0 + 1)
