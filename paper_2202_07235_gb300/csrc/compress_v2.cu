@@ -37,7 +37,6 @@ struct C2Split<512> {
   static constexpr int P1 = 32, P2 = 16;
 };
 
-constexpr int kNT = 256;
 constexpr int kBufBudget = 96 * 1024;
 
 constexpr int imax(int a, int b) { return a > b ? a : b; }
@@ -47,14 +46,17 @@ struct C2Cfg {
   static constexpr int M = Q / 2, P1 = C2Split<Q>::P1, P2 = C2Split<Q>::P2, XP = P2 + 1, RR = P1 / P2;
   static constexpr int SEQ = imax(Q, P1 * XP);                         // float2 per sequence buffer
   static constexpr int TG = imax(1, kBufBudget / (HB * SEQ * 8));      // translations per group
+  // threads: one projection item (translation, angle) each when TG * M allows
+  static constexpr int NT = (TG * M) % 384 == 0 ? 384 : 256;
   static size_t smem(int R) {
     return (size_t)R * M * 8 + (size_t)R * HB * 8 + (size_t)Q * 8 + (size_t)TG * HB * SEQ * 8;
   }
 };
 
 template <int Q, int HB>
-__global__ void __launch_bounds__(kNT) compress2_kernel(const __grid_constant__ Compress2Params p) {
+__global__ void __launch_bounds__(C2Cfg<Q, HB>::NT) compress2_kernel(const __grid_constant__ Compress2Params p) {
   using C = C2Cfg<Q, HB>;
+  constexpr int kNT = C::NT;
   constexpr int M = C::M, P1 = C::P1, P2 = C::P2, XP = C::XP, RR = C::RR, SEQ = C::SEQ, TG = C::TG;
   static_assert(HB % 2 == 0, "HB must be even");
   extern __shared__ __align__(16) unsigned char c2_smem[];
@@ -66,10 +68,23 @@ __global__ void __launch_bounds__(kNT) compress2_kernel(const __grid_constant__ 
   const int n = blockIdx.x, tid = threadIdx.x;
   if (n >= p.N) return;
 
+  // stage the half rings with asynchronous 16-byte copies (two samples each), all
+  // in flight at once; M is even and every ring starts 16-byte aligned when the
+  // array does, else plain loads
   const float2* src = p.polar + (size_t)n * R * Q;
-  for (int i = tid; i < R * M; i += kNT) {
-    const int r = i / M, psi = i % M;
-    img[i] = src[(size_t)r * Q + psi];
+  if (((uintptr_t)p.polar & 15u) == 0) {
+    for (int i = tid; i < R * M / 2; i += kNT) {
+      const int r = (2 * i) / M, psi = (2 * i) % M;
+      const unsigned d = (unsigned)__cvta_generic_to_shared(img + 2 * i);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + (size_t)r * Q + psi) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  } else {
+    for (int i = tid; i < R * M; i += kNT) {
+      const int r = i / M, psi = i % M;
+      img[i] = src[(size_t)r * Q + psi];
+    }
   }
   for (int i = tid; i < P1 * P2; i += kNT) {
     const int k1 = i / P2, t = i % P2;
@@ -207,7 +222,7 @@ int launch_q(const Compress2Params& p, cudaStream_t stream) {
     if (cudaFuncSetAttribute(compress2_kernel<Q, HB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return RSVD_ECUDA;
-    compress2_kernel<Q, HB><<<p.N, kNT, smem, stream>>>(p);
+    compress2_kernel<Q, HB><<<p.N, C::NT, smem, stream>>>(p);
     return launch_status();
   };
   if (H <= 4) return go(std::integral_constant<int, 4>{});
