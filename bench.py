@@ -494,7 +494,7 @@ def run_gradient(args):
     from synthetic import CONFIGS, make_workload_torch
 
     rank, world, local = _dist_env()
-    cfg = dict(CONFIGS["gradient"])
+    cfg = dict(CONFIGS["gradient" if args.config == "gradient" else args.config])
     if args.n_images:
         cfg["N_A"] = args.n_images
     torch.cuda.set_device(local)
@@ -565,10 +565,10 @@ def run_gradient(args):
         "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": elapsed / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
-        "config": {"workload": "differentiation: " + _workload_desc(cfg), "inv_sigma2": 1.0,
+        "config": {"workload": "differentiation: " + _workload_desc(cfg), "inv_sigma2": 1.0, "N_A_per_gpu": N_A,
                    "breakdown_ms": {"compress": round(part[0], 3), "forward_align_lse": round(part[1], 3),
                                     "lse_backward": round(part[2], 3), "compress_backward": round(part[3], 3)}},
-        "roofline": {"bound": "alu", "kernel": "grad_kernel<128,12> (both roles)", "achieved": round(achieved, 2),
+        "roofline": {"bound": "alu", "kernel": f"grad_kernel<{Q // 2},{H}> (both roles)", "achieved": round(achieved, 2),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None},
         "gpu_launches": 9 * K,
     }
@@ -1287,6 +1287,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
                     help="operand precision of the scoring contraction (tensor cores unless fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--backward", action="store_true",
+                    help="time forward + log-sum-exp backward on --config's geometry (as --config gradient)")
     ap.add_argument("--no-forms", action="store_true", help="skip the tensor-core operand forms")
     ap.add_argument("--cpu-images", type=int, default=0, help="images in the cpu_baseline sample (0 = auto)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target wall time of the cpu_baseline sample")
@@ -1302,7 +1304,7 @@ def main():
         run_reference_volumes(args)
     elif args.impl == "reference":
         run_reference(args)
-    elif args.config == "gradient":
+    elif args.config == "gradient" or args.backward:
         run_gradient(args)
     elif args.config == "volumes":
         run_volumes(args)
