@@ -881,7 +881,7 @@ def run_rows(args):
         out.update({"metric": "pair·translation·rotation scores/sec (17 CTF groups)", "value": pairs * Q / (ms / 1e3),
                     "unit": "scores/s", "ms_per_step": ms, "higher_is_better": True,
                     "config": {"workload": "f3 per-CTF groups: " + _workload_desc(cfg) + f", G={G} groups"},
-                    "roofline": {"bound": "alu", "kernel": "ws_align_kernel<128,12> (17 launches)",
+                    "roofline": {"bound": "alu", "kernel": "ws_align_kernel<128,12> (17 launches on 4 streams)",
                                  "achieved": round(pairs * _alg_flops_per_pair(H, Q) / (ms / 1e3) / 1e12, 2),
                                  "peak": round(peak_alu, 2), "unit": "TFLOP/s",
                                  "frac": round(pairs * _alg_flops_per_pair(H, Q) / (ms / 1e3) / 1e12 / peak_alu, 4),

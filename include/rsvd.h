@@ -394,6 +394,25 @@ int rsvd_align_best_host(int R, int Q, const double* k, const double* w, const d
                          int N_B, int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
                          int chunk, void* workspace, size_t workspace_bytes, void* stream, void* copy_stream);
 
+/* ------------------------------------------------------------------------
+ * Per-CTF-group alignment (section 3.5), with U and U_targets from
+ * rsvd_build_radial_svd_grouped (dev double [G][R][H] each): the images of
+ * group g, rows offsets[g] .. offsets[g+1]-1 of images (dev complex64
+ * [N_A][R][Q]; offsets host int [G+1], non-decreasing), are compressed with U[g]
+ * and aligned against the templates (dev complex64 [N_B][R][Q]) compressed
+ * with U_targets[g]; best/arg dev [N_A][N_B] as rsvd_align_best. Group g runs
+ * on streams[g mod n_streams] (distinct streams, n_streams >= 1); the other
+ * streams first wait for the work queued on streams[0], which waits for them
+ * at the end. workspace >= rsvd_align_grouped_workspace_bytes(Q, H, T, N_B,
+ * largest group, precision, n_streams), 256-byte aligned.
+ * ------------------------------------------------------------------------ */
+size_t rsvd_align_grouped_workspace_bytes(int Q, int H, int T, int N_B, int max_group, int precision,
+                                          int n_streams);
+int rsvd_align_grouped(int R, int Q, const double* k, const double* w, const double* U, const double* U_targets,
+                       int H, const void* images, const int* offsets, int G, const double* deltas, int T,
+                       const void* templates, int N_B, int precision, float* best, int32_t* arg, void* workspace,
+                       size_t workspace_bytes, void* const* streams, int n_streams);
+
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).
  * Provided so callers can cross-check the fused kernel. */

@@ -18,6 +18,8 @@ _lib = None
 
 c_int, c_float, c_size_t, c_void_p = ctypes.c_int, ctypes.c_float, ctypes.c_size_t, ctypes.c_void_p
 c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int_p = ctypes.POINTER(ctypes.c_int)
+c_void_pp = ctypes.POINTER(ctypes.c_void_p)
 
 # name -> (restype, argtypes); mirrors include/rsvd.h
 SIGNATURES = {
@@ -54,6 +56,10 @@ SIGNATURES = {
     "rsvd_align_fine_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
     "rsvd_align_best_fine_shifted": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float,
                                              c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "rsvd_align_grouped_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
+    "rsvd_align_grouped": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_void_p, c_int, c_void_p,
+                                   c_int_p, c_int, c_double_p, c_int, c_void_p, c_int, c_int, c_void_p,
+                                   c_void_p, c_void_p, c_size_t, c_void_pp, c_int]),
     "rsvd_align_host_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
     "rsvd_align_best_host": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_void_p, c_int,
                                      c_double_p, c_int, c_void_p, c_int, c_int, c_float, c_void_p, c_void_p,

@@ -136,25 +136,52 @@ def build_radial_svd_grouped(w, templates: torch.Tensor, ctf: torch.Tensor, H: i
     return U, Ut, eig
 
 
+_group_streams: dict = {}
+
+
 def align_grouped(k, w, images: torch.Tensor, offsets, templates: torch.Tensor, U: torch.Tensor,
-                  U_targets: torch.Tensor, deltas=None, precision=FP32, stream=None):
+                  U_targets: torch.Tensor, deltas=None, precision=FP32, n_streams: int = 4, workspace=None,
+                  stream=None):
     """Align the images of each CTF group (rows offsets[g] .. offsets[g+1]-1) to
-    that group's corrected targets: compress both with the group's vectors and
-    run align_best per group. Returns best [N_A, N_B], arg [N_A, N_B]."""
-    N_A = images.shape[0]
-    N_B, R, Q = templates.shape
-    H = U.shape[2]
-    T = 1 if deltas is None else np.asarray(deltas).reshape(-1, 2).shape[0]
-    best = torch.empty((N_A, N_B), dtype=torch.float32, device=images.device)
-    arg = torch.empty((N_A, N_B), dtype=torch.int32, device=images.device)
-    for g in range(U.shape[0]):
-        a0, a1 = int(offsets[g]), int(offsets[g + 1])
-        if a1 <= a0:
-            continue
-        cA = compress(k, w, U[g], images[a0:a1], deltas=deltas, precision=precision, stream=stream)
-        cB = compress(k, w, U_targets[g], templates, precision=precision, stream=stream)
-        align_best(cA, a1 - a0, T, cB, N_B, H, Q, precision=precision, out=(best[a0:a1], arg[a0:a1], None),
-                   stream=stream)
+    that group's corrected targets (rsvd_align_grouped): both compressed with the
+    group's vectors, groups spread over n_streams streams (the first is `stream`).
+    Returns best [N_A, N_B], arg [N_A, N_B]."""
+    precision = _prec(precision)
+    _require_cuda(images, torch.complex64, "images")
+    _require_cuda(templates, torch.complex64, "templates")
+    _require_cuda(U, torch.float64, "U")
+    _require_cuda(U_targets, torch.float64, "U_targets")
+    N_A, R, Q = images.shape
+    N_B = templates.shape[0]
+    G, _, H = U.shape
+    ka, kp = _host_f64(k)
+    wa, wp = _host_f64(w)
+    if deltas is None:
+        T, dp, da = 1, None, None
+    else:
+        da, dp = _host_f64(deltas)
+        T = da.reshape(-1, 2).shape[0]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    if off.shape != (G + 1,) or off[0] != 0 or off[-1] != N_A:
+        raise ValueError("offsets must be [G+1] from 0 to N_A")
+    max_group = int(np.max(np.diff(off)))
+    dev = images.device
+    best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
+    arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
+    if max_group == 0:
+        return best, arg
+    need = int(lib().rsvd_align_grouped_workspace_bytes(Q, H, T, N_B, max_group, precision, n_streams))
+    if need == 0:
+        raise ValueError("unsupported sizes for grouped alignment")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    s0 = stream if stream is not None else torch.cuda.current_stream()
+    extra = _group_streams.setdefault((dev, n_streams), [torch.cuda.Stream(device=dev) for _ in range(n_streams - 1)])
+    handles = (ctypes.c_void_p * n_streams)(int(s0.cuda_stream), *[int(x.cuda_stream) for x in extra])
+    check(lib().rsvd_align_grouped(R, Q, kp, wp, _ptr(U), _ptr(U_targets), H, _ptr(images),
+                                   off.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), G, dp, T, _ptr(templates), N_B,
+                                   precision, _ptr(best), _ptr(arg), _ptr(workspace), workspace.numel(), handles,
+                                   n_streams), "rsvd_align_grouped")
     return best, arg
 
 

@@ -141,3 +141,97 @@ extern "C" int rsvd_align_best_host(int R, int Q, const double* k, const double*
   if (cudaStreamWaitEvent(st, ev_back[(nchunk - 1) & 1], 0) != cudaSuccess) return RSVD_ECUDA;
   return RSVD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Per-CTF-group alignment (section 3.5): the images of group g (rows
+// offsets[g] .. offsets[g+1]-1) against the templates compressed with the
+// group's target vectors, each group compressed and aligned on one of the
+// caller's streams (round robin), so that consecutive groups' kernels overlap
+// instead of each launch ending in a partly filled wave.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GroupLayout {
+  size_t cA, cB, per_stream;
+};
+
+GroupLayout group_layout(int Q, int H, int T, int N_B, int max_group, int precision) {
+  GroupLayout L{};
+  L.cA = up(rsvd_compressed_bytes(max_group, T, H, Q, precision));
+  L.cB = up(rsvd_compressed_bytes(N_B, 1, H, Q, precision));
+  L.per_stream = L.cA + L.cB;
+  return L;
+}
+
+}  // namespace
+
+extern "C" size_t rsvd_align_grouped_workspace_bytes(int Q, int H, int T, int N_B, int max_group, int precision,
+                                                     int n_streams) {
+  if (Q <= 0 || H <= 0 || T <= 0 || N_B <= 0 || max_group <= 0 || n_streams <= 0) return 0;
+  if (rsvd_compressed_bytes(max_group, T, H, Q, precision) == 0) return 0;
+  return group_layout(Q, H, T, N_B, max_group, precision).per_stream * (size_t)n_streams;
+}
+
+extern "C" int rsvd_align_grouped(int R, int Q, const double* k, const double* w, const double* U,
+                                  const double* U_targets, int H, const void* images, const int* offsets, int G,
+                                  const double* deltas, int T, const void* templates, int N_B, int precision,
+                                  float* best, int32_t* arg, void* workspace, size_t workspace_bytes,
+                                  void* const* streams, int n_streams) {
+  if (!k || !w || !U || !U_targets || !images || !offsets || !templates || !best || !arg || !streams || R <= 0 ||
+      Q <= 0 || H <= 0 || G <= 0 || T <= 0 || N_B <= 0 || n_streams <= 0 || (T > 1 && !deltas))
+    return RSVD_EINVAL;
+  int max_group = 0;
+  for (int g = 0; g < G; ++g) {
+    if (offsets[g + 1] < offsets[g] || offsets[g] < 0) return RSVD_EINVAL;
+    max_group = max(max_group, offsets[g + 1] - offsets[g]);
+  }
+  if (max_group == 0) return RSVD_OK;
+  for (int i = 0; i < n_streams; ++i)
+    for (int j = 0; j < i; ++j)
+      if (streams[i] == streams[j]) return RSVD_EINVAL;
+  const size_t need = rsvd_align_grouped_workspace_bytes(Q, H, T, N_B, max_group, precision, n_streams);
+  if (need == 0) return RSVD_EUNSUPPORTED;
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & (kAlign - 1))) return RSVD_EWORKSPACE;
+  const GroupLayout L = group_layout(Q, H, T, N_B, max_group, precision);
+  cudaStream_t s0 = static_cast<cudaStream_t>(streams[0]);
+  cudaEvent_t ev[64];
+  const int ns = n_streams < 64 ? n_streams : 64;
+  int made = 0;
+  auto cleanup = [&]() {
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  };
+  for (; made < ns; ++made)
+    if (cudaEventCreateWithFlags(&ev[made], cudaEventDisableTiming) != cudaSuccess) {
+      cleanup();
+      return RSVD_ECUDA;
+    }
+  // fork: every stream starts after the work already queued on the first
+  int rc = RSVD_OK;
+  if (cudaEventRecord(ev[0], s0) != cudaSuccess) rc = RSVD_ECUDA;
+  for (int i = 1; i < ns && rc == RSVD_OK; ++i)
+    if (cudaStreamWaitEvent(static_cast<cudaStream_t>(streams[i]), ev[0], 0) != cudaSuccess) rc = RSVD_ECUDA;
+  const size_t ring = (size_t)R * Q * sizeof(float2);
+  const size_t uH = (size_t)R * H;
+  for (int g = 0; g < G && rc == RSVD_OK; ++g) {
+    const int a0 = offsets[g], n = offsets[g + 1] - a0;
+    if (n == 0) continue;
+    const int si = g % ns;
+    void* st = streams[si];
+    char* cA = static_cast<char*>(workspace) + (size_t)si * L.per_stream;
+    char* cB = cA + L.cA;
+    rc = rsvd_compress(R, Q, k, w, U + g * uH, H, static_cast<const char*>(images) + (size_t)a0 * ring, n, deltas, T,
+                       precision, cA, st);
+    if (rc == RSVD_OK) rc = rsvd_compress(R, Q, k, w, U_targets + g * uH, H, templates, N_B, nullptr, 1, precision, cB, st);
+    if (rc == RSVD_OK)
+      rc = rsvd_align_best(cA, n, T, cB, N_B, H, Q, precision, 1.0f, best + (size_t)a0 * N_B, arg + (size_t)a0 * N_B,
+                           nullptr, st);
+  }
+  // join: the first stream waits for all the others
+  for (int i = 1; i < ns; ++i) {
+    if (cudaEventRecord(ev[i], static_cast<cudaStream_t>(streams[i])) != cudaSuccess ||
+        cudaStreamWaitEvent(s0, ev[i], 0) != cudaSuccess)
+      if (rc == RSVD_OK) rc = RSVD_ECUDA;
+  }
+  cleanup();
+  return rc;
+}

@@ -67,3 +67,22 @@ def test_grouped_alignment_recovers_noiseless_truth():
     best, arg = best.cpu().numpy(), arg.cpu().numpy()
     assert np.array_equal(np.argmax(best, axis=1), wl.truth_j)
     assert np.array_equal(arg[np.arange(15), wl.truth_j], wl.truth_m)
+
+
+def test_grouped_alignment_is_the_same_on_any_number_of_streams():
+    """Groups on 1 or 4 streams (round robin), including an empty and an odd-sized
+    group, give bit-identical results: each group's kernels are independent."""
+    wl = make_grouped_workload(N=128, R=64, Q=256, N_B=11, N_A=29, G=5, snr=0.1, T_side=3, seed=12)
+    g = wl.grid
+    S = torch.from_numpy(wl.templates.astype(np.complex64)).to(DEV)
+    A = torch.from_numpy(wl.images.astype(np.complex64)).to(DEV)
+    U, Ut, _ = P.build_radial_svd_grouped(g.w, S, torch.from_numpy(wl.ctf).to(DEV), 12)
+    off = np.array([0, 7, 7, 18, 19, 29])  # group 1 empty, group 3 a single image
+    b1, a1 = P.align_grouped(g.k, g.w, A, off, S, U, Ut, deltas=wl.deltas, n_streams=1)
+    b4, a4 = P.align_grouped(g.k, g.w, A, off, S, U, Ut, deltas=wl.deltas, n_streams=4)
+    P.status()
+    assert torch.equal(b1, b4) and torch.equal(a1, a4)
+    X = O.grouped_scores(wl.images.astype(np.complex64).astype(np.complex128), off,
+                         wl.templates.astype(np.complex64).astype(np.complex128), wl.ctf, U.cpu().numpy(), g.w, g.k,
+                         wl.deltas)
+    check_best(X, b4.cpu().numpy(), a4.cpu().numpy())
