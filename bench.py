@@ -1069,19 +1069,23 @@ def run_volumes(args):
     rot = nb * Mp * Mp
     scores_step = N_A * N_B * rot
 
-    # end to end: volumes and target from pinned host memory, best/arg back
+    # end to end through the host-input call (rsvd_align_volumes_host): volumes and
+    # target from pinned host memory in chunks overlapping the kernels, best/arg back
     vols_h = vols.cpu().pin_memory()
     tgt_h = tgt.cpu().pin_memory()
     best_h = torch.empty(best.shape, dtype=best.dtype).pin_memory()
     arg_h = torch.empty(arg.shape, dtype=arg.dtype).pin_memory()
-    vols_d = torch.empty_like(vols)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    chunk = min(N_A, 8 * sm_count)
+    del cA
+    torch.cuda.empty_cache()
+    ws_host = torch.empty(P.lib().rsvd_align_volumes_host_workspace_bytes(g.R, L, HC, N_B, chunk), dtype=torch.uint8,
+                          device=dev)
+    copy_stream = torch.cuda.Stream(device=dev)
 
     def e2e_step():
-        vols_d.copy_(vols_h, non_blocking=True)
-        tgt.copy_(tgt_h, non_blocking=True)
-        step(None, vols_d)
-        best_h.copy_(best, non_blocking=True)
-        arg_h.copy_(arg, non_blocking=True)
+        P.align_volumes_host(g.w, U, Vd, tables, Mp, vols_h, tgt_h, chunk=chunk, workspace=ws_host,
+                             out=(best_h, arg_h), stream=stream, copy_stream=copy_stream)
 
     K2 = max(3, min(K, 10))
     for _ in range(2):

@@ -413,6 +413,21 @@ int rsvd_align_grouped(int R, int Q, const double* k, const double* w, const dou
                        const void* templates, int N_B, int precision, float* best, int32_t* arg, void* workspace,
                        size_t workspace_bytes, void* const* streams, int n_streams);
 
+/* Host-input volume alignment: volumes host complex64 [N_A][R][L+1][2L+1] and
+ * targets host [N_B][R][L+1][2L+1] (pinned for the copies to overlap), U, V and
+ * tables on the device as for rsvd_compress_volume and rsvd_align_volumes;
+ * best, arg host [N_A][N_B]. The targets are copied and compressed first, then
+ * the volumes in chunks of `chunk` on copy_stream (a stream other than
+ * `stream`), the copy of chunk c + 1 overlapping the work on chunk c. Returns
+ * after enqueueing; `stream` waits for the last copy back. workspace >=
+ * rsvd_align_volumes_host_workspace_bytes(R, L, H_C, N_B, chunk), device,
+ * 256-byte aligned. */
+size_t rsvd_align_volumes_host_workspace_bytes(int R, int L, int HC, int N_B, int chunk);
+int rsvd_align_volumes_host(int R, int L, const double* w, const double* U, int HC, const double* V, int HD,
+                            const float* tables, int n_beta, int Mp, const void* volumes, int N_A, const void* targets,
+                            int N_B, float* best, int32_t* arg, int chunk, void* workspace, size_t workspace_bytes,
+                            void* stream, void* copy_stream);
+
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).
  * Provided so callers can cross-check the fused kernel. */

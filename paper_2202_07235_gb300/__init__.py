@@ -20,6 +20,7 @@ from .api import (  # noqa: F401
     align_scores,
     align_scores_fine,
     align_volumes,
+    align_volumes_host,
     build_radial_svd,
     build_volume_svd,
     build_radial_svd_grouped,

@@ -318,6 +318,42 @@ def align_best_host(k, w, U: torch.Tensor, images: torch.Tensor, templates: torc
     return best, arg, lse
 
 
+def align_volumes_host(w, U: torch.Tensor, V: torch.Tensor, tables: torch.Tensor, Mp: int, volumes: torch.Tensor,
+                       targets: torch.Tensor, chunk: int | None = None, workspace=None, out=None, stream=None,
+                       copy_stream=None):
+    """rsvd_align_volumes_host: volumes complex64 [N_A, R, L+1, 2L+1] and targets
+    [N_B, ...] in host memory (pinned for overlap); returns host (best, arg) after
+    synchronising `stream`."""
+    _require_host(volumes, torch.complex64, "volumes")
+    _require_host(targets, torch.complex64, "targets")
+    _require_cuda(U, torch.float64, "U")
+    _require_cuda(V, torch.float64, "V")
+    _require_cuda(tables, torch.float32, "tables")
+    N_A, R, L1, M = volumes.shape
+    N_B = targets.shape[0]
+    HC, HD = U.shape[1], V.shape[1]
+    wa, wp = _host_f64(w)
+    if chunk is None:
+        chunk = 8 * torch.cuda.get_device_properties(U.device).multi_processor_count
+    chunk = max(1, min(int(chunk), N_A))
+    need = int(lib().rsvd_align_volumes_host_workspace_bytes(R, L1 - 1, HC, N_B, chunk))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=U.device)
+    if out is None:
+        best = torch.empty((N_A, N_B), dtype=torch.float32).pin_memory()
+        arg = torch.empty((N_A, N_B), dtype=torch.int32).pin_memory()
+    else:
+        best, arg = out
+    s = stream if stream is not None else torch.cuda.current_stream()
+    cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=U.device)
+    check(lib().rsvd_align_volumes_host(R, L1 - 1, wp, _ptr(U), HC, _ptr(V), HD, _ptr(tables), tables.shape[0], Mp,
+                                        _ptr(volumes), N_A, _ptr(targets), N_B, _ptr(best), _ptr(arg), chunk,
+                                        _ptr(workspace), workspace.numel(), int(s.cuda_stream), int(cs.cuda_stream)),
+          "rsvd_align_volumes_host")
+    s.synchronize()
+    return best, arg
+
+
 def compressed_bytes(N: int, T: int, H: int, Q: int, precision=FP32) -> int:
     return int(lib().rsvd_compressed_bytes(N, T, H, Q, _prec(precision)))
 

@@ -235,3 +235,103 @@ extern "C" int rsvd_align_grouped(int R, int Q, const double* k, const double* w
   cleanup();
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Host-input volume alignment (section 4): volumes and targets in (pinned) host
+// memory, best/arg back to host memory; the copy of chunk c + 1 of the volumes
+// overlaps the compression and alignment of chunk c, with the same buffers and
+// events as the image pipeline above.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct VolPipeLayout {
+  size_t vol, tgt, cA, cB, best, arg, total;
+};
+
+VolPipeLayout vol_pipe_layout(int R, int L, int HC, int N_B, int chunk) {
+  VolPipeLayout P{};
+  const size_t lm = (size_t)(L + 1) * (2 * L + 1) * sizeof(float2);
+  P.vol = up((size_t)chunk * R * lm);
+  P.tgt = up((size_t)N_B * R * lm);
+  P.cA = up((size_t)chunk * HC * lm);
+  P.cB = up((size_t)N_B * HC * lm);
+  const size_t outs = (size_t)chunk * N_B;
+  P.best = up(outs * sizeof(float));
+  P.arg = up(outs * sizeof(int32_t));
+  P.total = 2 * P.vol + P.tgt + P.cA + P.cB + 2 * (P.best + P.arg);
+  return P;
+}
+
+}  // namespace
+
+extern "C" size_t rsvd_align_volumes_host_workspace_bytes(int R, int L, int HC, int N_B, int chunk) {
+  if (R <= 0 || L < 1 || HC <= 0 || N_B <= 0 || chunk <= 0) return 0;
+  return vol_pipe_layout(R, L, HC, N_B, chunk).total;
+}
+
+extern "C" int rsvd_align_volumes_host(int R, int L, const double* w, const double* U, int HC, const double* V, int HD,
+                                       const float* tables, int n_beta, int Mp, const void* volumes, int N_A,
+                                       const void* targets, int N_B, float* best, int32_t* arg, int chunk,
+                                       void* workspace, size_t workspace_bytes, void* stream, void* copy_stream) {
+  if (!w || !U || !V || !tables || !volumes || !targets || !best || !arg || R <= 0 || L < 1 || HC <= 0 || HD <= 0 ||
+      n_beta <= 0 || N_A <= 0 || N_B <= 0 || chunk <= 0)
+    return RSVD_EINVAL;
+  if (stream == copy_stream) return RSVD_EINVAL;
+  chunk = chunk < N_A ? chunk : N_A;
+  const size_t need = rsvd_align_volumes_host_workspace_bytes(R, L, HC, N_B, chunk);
+  if (need == 0) return RSVD_EUNSUPPORTED;
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & (kAlign - 1))) return RSVD_EWORKSPACE;
+  const VolPipeLayout P = vol_pipe_layout(R, L, HC, N_B, chunk);
+  char* ws = static_cast<char*>(workspace);
+  char* vol[2] = {ws, ws + P.vol};
+  char* tgt = ws + 2 * P.vol;
+  char* cA = tgt + P.tgt;
+  char* cB = cA + P.cA;
+  char* outb = cB + P.cB;
+  float* best_d[2];
+  int32_t* arg_d[2];
+  for (int b = 0; b < 2; ++b) {
+    best_d[b] = reinterpret_cast<float*>(outb + b * (P.best + P.arg));
+    arg_d[b] = reinterpret_cast<int32_t*>(outb + b * (P.best + P.arg) + P.best);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream), cp = static_cast<cudaStream_t>(copy_stream);
+  Events E;
+  if (!E.make()) return RSVD_ECUDA;
+  cudaEvent_t ev_in[2] = {E.ev[0], E.ev[1]}, ev_used[2] = {E.ev[2], E.ev[3]};
+  cudaEvent_t ev_done[2] = {E.ev[4], E.ev[5]}, ev_back[2] = {E.ev[6], E.ev[7]};
+  const size_t per = (size_t)R * (L + 1) * (2 * L + 1) * sizeof(float2);  // one volume
+  if (cudaMemcpyAsync(tgt, targets, (size_t)N_B * per, cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+      cudaEventRecord(ev_back[1], cp) != cudaSuccess || cudaStreamWaitEvent(st, ev_back[1], 0) != cudaSuccess)
+    return RSVD_ECUDA;
+  int rc = rsvd_compress_volume(R, L, w, U, HC, tgt, N_B, cB, stream);
+  if (rc != RSVD_OK) return rc;
+  const int nchunk = (N_A + chunk - 1) / chunk;
+  auto copy_in = [&](int c) -> int {
+    const int b = c & 1, n0 = c * chunk, n = min(chunk, N_A - n0);
+    if (c >= 2 && cudaStreamWaitEvent(cp, ev_used[b], 0) != cudaSuccess) return RSVD_ECUDA;
+    if (cudaMemcpyAsync(vol[b], static_cast<const char*>(volumes) + (size_t)n0 * per, (size_t)n * per,
+                        cudaMemcpyHostToDevice, cp) != cudaSuccess)
+      return RSVD_ECUDA;
+    return cudaEventRecord(ev_in[b], cp) == cudaSuccess ? RSVD_OK : RSVD_ECUDA;
+  };
+  if ((rc = copy_in(0)) != RSVD_OK) return rc;
+  for (int c = 0; c < nchunk; ++c) {
+    const int b = c & 1, n0 = c * chunk, n = min(chunk, N_A - n0);
+    if (c + 1 < nchunk && (rc = copy_in(c + 1)) != RSVD_OK) return rc;
+    if (cudaStreamWaitEvent(st, ev_in[b], 0) != cudaSuccess) return RSVD_ECUDA;
+    if ((rc = rsvd_compress_volume(R, L, w, U, HC, vol[b], n, cA, stream)) != RSVD_OK) return rc;
+    if (cudaEventRecord(ev_used[b], st) != cudaSuccess) return RSVD_ECUDA;
+    if (c >= 2 && cudaStreamWaitEvent(st, ev_back[b], 0) != cudaSuccess) return RSVD_ECUDA;
+    rc = rsvd_align_volumes(cA, n, cB, N_B, HC, L, V, HD, tables, n_beta, Mp, best_d[b], arg_d[b], stream);
+    if (rc != RSVD_OK) return rc;
+    if (cudaEventRecord(ev_done[b], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev_done[b], 0) != cudaSuccess)
+      return RSVD_ECUDA;
+    const size_t outs = (size_t)n * N_B, o = (size_t)n0 * N_B;
+    if (cudaMemcpyAsync(best + o, best_d[b], outs * sizeof(float), cudaMemcpyDeviceToHost, cp) != cudaSuccess ||
+        cudaMemcpyAsync(arg + o, arg_d[b], outs * sizeof(int32_t), cudaMemcpyDeviceToHost, cp) != cudaSuccess ||
+        cudaEventRecord(ev_back[b], cp) != cudaSuccess)
+      return RSVD_ECUDA;
+  }
+  if (cudaStreamWaitEvent(st, ev_back[(nchunk - 1) & 1], 0) != cudaSuccess) return RSVD_ECUDA;
+  return RSVD_OK;
+}

@@ -146,3 +146,18 @@ def test_volume_limits_are_refused():
     with pytest.raises(P.RSVDError):  # H_D above the limit
         P.volume_tables(torch.zeros((L + 1, 9), dtype=torch.float64, device=DEV), [0.0, 1.0])
     P.status()
+
+
+def test_volume_host_pipeline_equals_device_path():
+    wl, A, B = _wl(L=12, R=10, N_B=3, N_A=23, n_beta=7, Mp=32, seed=21)
+    g = wl.grid
+    U, _, Vd, _ = P.build_volume_svd(g.w, torch.from_numpy(B).to(DEV), 8, 8)
+    T = P.volume_tables(Vd, wl.betas)
+    cA = P.compress_volume(g.w, U, torch.from_numpy(A).to(DEV))
+    cB = P.compress_volume(g.w, U, torch.from_numpy(B).to(DEV))
+    bd, ad = P.align_volumes(cA, cB, Vd, T, 32)
+    bh, ah = P.align_volumes_host(g.w, U, Vd, T, 32, torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(),
+                                  chunk=5)
+    P.status()
+    assert np.array_equal(bh.numpy(), bd.cpu().numpy())
+    assert np.array_equal(ah.numpy(), ad.cpu().numpy())
