@@ -102,3 +102,32 @@ def test_argument_errors_return_codes_without_a_gpu(lib):
     h = lib.rsvd_build_radial_svd
     h.restype, h.argtypes = SIGNATURES["rsvd_build_radial_svd"]
     assert h(4, 16, ctypes.cast(k, ctypes.POINTER(ctypes.c_double)), one, 3, 2, one, one, None, 0, None) == -6
+
+
+def test_empty_inputs_are_argument_errors(lib):
+    """Zero objects are an argument error (RSVD_EINVAL) and nothing is enqueued:
+    the checks run before any CUDA call, so this holds without a GPU."""
+    from paper_2202_07235_gb300._native import SIGNATURES
+
+    def fn(name):
+        f = getattr(lib, name)
+        f.restype, f.argtypes = SIGNATURES[name]
+        return f
+
+    one = ctypes.c_void_p(256)
+    k = (ctypes.c_double * 4)(1, 2, 3, 4)
+    kp = ctypes.cast(k, ctypes.POINTER(ctypes.c_double))
+    assert fn("rsvd_align_best")(one, 0, 1, one, 1, 8, 256, 0, 1.0, one, one, None, None) == -1
+    assert fn("rsvd_align_best")(one, 1, 1, one, 0, 8, 256, 0, 1.0, one, one, None, None) == -1
+    assert fn("rsvd_align_scores")(one, 0, 1, one, 1, 8, 256, 0, one, None) == -1
+    assert fn("rsvd_compress")(4, 16, kp, kp, one, 2, one, 0, None, 1, 0, one, None) == -1
+    assert fn("rsvd_align_best_fine_shifted")(one, 0, 1, one, 1, 8, 256, 2, 1.0, one, one, None, one, 1 << 20,
+                                              None) == -1
+    assert fn("rsvd_align_best_host")(4, 16, kp, kp, one, 2, one, 0, None, 1, one, 1, 0, 1.0, one, one, None, 8, one,
+                                      1 << 20, one, None) == -1
+    assert fn("rsvd_align_volumes")(one, 0, one, 1, 4, 8, one, 4, one, 1, 32, one, one, None) == -1
+    assert fn("rsvd_compress_volume")(4, 8, kp, one, 2, one, 0, one, None) == -1
+    offs = (ctypes.c_int * 2)(0, 0)
+    streams = (ctypes.c_void_p * 1)(None)
+    assert fn("rsvd_align_grouped")(4, 16, kp, kp, one, one, 2, one, offs, 0, None, 1, one, 1, 0, one, one, one,
+                                    1 << 20, streams, 1) == -1

@@ -205,3 +205,16 @@ def test_throughput_workload_sampled_parity():
     a = arg.cpu().numpy()[np.ix_(ns, js)]
     l_ = lse.cpu().numpy()[np.ix_(ns, js)]
     check_best(Xr, b, a, l_, 1.0)
+
+
+def test_maximum_sizes_match_oracle():
+    """The largest documented sizes together: R = 256 rings, H = 64 vectors,
+    Q = 1024 angles, T = 64 translations (8 x 8 grid)."""
+    R, Q, H = 256, 1024, 64
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=3, N_A=2, T_side=8, H=H, seed=31)
+    cA, cB, T = _gpu(wl, A, B, U)
+    assert T == 64
+    best, arg, lse = P.align_best(cA, 2, T, cB, 3, H, Q, want_lse=True)
+    P.status()
+    X, _, _ = oracle_scores(wl, A, B, U)
+    check_best(X, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
