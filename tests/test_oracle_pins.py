@@ -305,3 +305,23 @@ def test_fine_grid_matches_the_definition_at_an_off_grid_rotation():
     direct = float(np.real(np.sum(grid.w[:, None] * np.conj(A[0]) * B_rot[0])) * grid.dpsi)
     assert int(np.argmax(Xf)) == 2 * m0 + 1
     assert abs(Xf[2 * m0 + 1] - direct) <= 1e-8 * abs(direct)
+
+
+def test_finer_grid_is_coarse_landscape_of_shifted_templates():
+    """The zero-padded landscape at gamma_m + 2 pi p / (P Q) equals the coarse
+    landscape of the templates rotated by p/P of a grid step in the compressed
+    domain, b(q) e^{-i q 2 pi p / (P Q)} for 0 < |q| < Q/2 with the Nyquist
+    coefficient scaled by cos(pi p / P): the identity the shifted GPU passes use."""
+    wl = make_workload(N=32, R=8, Q=16, N_B=3, N_A=2, snr=0.3, T_side=1, seed=3)
+    U, _ = O.principal_vectors(O.radial_kernel(wl.templates, wl.grid.w), 4)
+    a = O.compress(O.translate(wl.images, wl.grid.k, wl.deltas), U, wl.grid.w)
+    b = O.compress(wl.templates, U, wl.grid.w)
+    Q = b.shape[-1]
+    qs = np.where(np.arange(Q) < Q // 2, np.arange(Q), np.arange(Q) - Q)
+    for P_ in (2, 3, 4):
+        Xf = O.scores_fine(a, b, P_)
+        for p in range(P_):
+            bp = b * np.exp(-1j * qs * 2 * math.pi * p / (P_ * Q))
+            bp[..., Q // 2] = b[..., Q // 2] * math.cos(math.pi * p / P_)
+            Xc = O.scores_compressed(a, bp).real
+            assert np.abs(Xc - Xf[..., p::P_]).max() <= 1e-12 * np.abs(Xf).max()

@@ -104,3 +104,14 @@ def test_kernels_drop_the_rotation_invariant_terms():
     B0 = np.zeros_like(B)
     B0[:, :, 0] = B[:, :, 0]  # only the l = 0 (rotation-invariant) content
     assert np.abs(V.volume_radial_kernel(B0, g.w)).max() == 0.0
+
+
+def test_wigner_d_mirror_symmetry():
+    """d^l_{-m1,-m2}(beta) = (-1)^{m1-m2} d^l_{m1,m2}(beta): with it the GPU's Hermitian
+    part of Step 1b gives Re X for any coefficients."""
+    for l in (1, 4, 11):
+        m = np.arange(-l, l + 1)
+        for beta in (0.3, 1.7, 2.9):
+            d = V.wigner_d(l, beta)
+            sign = (-1.0) ** (m[:, None] - m[None, :])
+            assert np.allclose(d[::-1, ::-1], sign * d, atol=1e-13)
