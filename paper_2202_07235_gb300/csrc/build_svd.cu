@@ -23,6 +23,8 @@
 #include "rsvd_internal.cuh"
 
 namespace rsvd {
+RSVD_HIDDEN int launch_jacobi(const double* C, double* A, double* V, int R, int H, double* U, double* eig, int batch,
+                              cudaStream_t st);
 namespace {
 
 constexpr int kTile = 64;       // C tile edge
@@ -290,6 +292,198 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_eig(const double* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Eigen-decomposition for R <= 64 with most of the work in FP32 (the part's
+// FP64 rate is 1/64 of its FP32 rate), finished in FP64: an FP32 cyclic Jacobi
+// gives an approximate eigenbasis V0; one FP64 Newton-Schulz step
+// V0 <- V0 (3 I - V0^T V0) / 2 makes it orthonormal to rounding; the FP64
+// Jacobi of the nearly diagonal A1 = V0^T C V0 (a couple of sweeps) gives V1,
+// and U = V0 V1 with the eigenvalues on the diagonal. Everything stays in
+// shared memory (four R x R FP64 buffers); one CTA per matrix.
+// ---------------------------------------------------------------------------
+constexpr int kMixedMaxR = 64;
+
+// Z = op(X) Y for R x R row-major matrices in shared memory (op = transpose if tx)
+__device__ __forceinline__ void smem_mm(const double* X, bool tx, const double* Y, double* Z, int R) {
+  for (int idx = threadIdx.x; idx < R * R; idx += blockDim.x) {
+    const int i = idx / R, j = idx % R;
+    double acc = 0.0;
+    if (tx) {
+      for (int k = 0; k < R; ++k) acc = fma(X[k * R + i], Y[k * R + j], acc);
+    } else {
+      for (int k = 0; k < R; ++k) acc = fma(X[i * R + k], Y[k * R + j], acc);
+    }
+    Z[idx] = acc;
+  }
+}
+
+// Cyclic Jacobi sweeps in precision F on symmetric A (R x R) accumulating V;
+// returns the number of sweeps run (max_sweeps if still rotating).
+template <typename F>
+__device__ int sym_jacobi(F* A, F* V, int R, int max_sweeps, F rel, F absfloor, F* cs_c, F* cs_s, int* pr_p,
+                          int* pr_q, int* rotated) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int n = (R % 2) ? R + 1 : R, npairs = n / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *rotated = 0;
+    __syncthreads();
+    for (int k = 0; k < n - 1; ++k) {
+      for (int i = tid; i < npairs; i += nth) {
+        int pp = rr_member(i, k, n), qq = rr_member(n - 1 - i, k, n);
+        if (pp > qq) {
+          const int tmp = pp;
+          pp = qq;
+          qq = tmp;
+        }
+        F c = 1, s = 0;
+        if (qq < R) {
+          const F apq = A[pp * R + qq], app = A[pp * R + pp], aqq = A[qq * R + qq];
+          if (fabs(apq) > fmax(rel * sqrt(fabs(app * aqq)), absfloor) && apq != F(0)) {
+            const F tau = (aqq - app) / (F(2) * apq);
+            const F t = (tau >= F(0) ? F(1) : F(-1)) / (fabs(tau) + sqrt(F(1) + tau * tau));
+            c = F(1) / sqrt(F(1) + t * t);
+            s = t * c;
+            *rotated = 1;
+          }
+        }
+        cs_c[i] = c;
+        cs_s[i] = s;
+        pr_p[i] = pp;
+        pr_q[i] = qq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * R; idx += nth) {  // A <- A J, V <- V J
+        const int i = idx / R, r = idx % R;
+        const int pp = pr_p[i], qq = pr_q[i];
+        if (qq >= R || cs_s[i] == F(0)) continue;
+        const F c = cs_c[i], s = cs_s[i];
+        const F ap = A[r * R + pp], aq = A[r * R + qq];
+        A[r * R + pp] = c * ap - s * aq;
+        A[r * R + qq] = s * ap + c * aq;
+        const F vp = V[r * R + pp], vq = V[r * R + qq];
+        V[r * R + pp] = c * vp - s * vq;
+        V[r * R + qq] = s * vp + c * vq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * R; idx += nth) {  // A <- J^T A
+        const int i = idx / R, col = idx % R;
+        const int pp = pr_p[i], qq = pr_q[i];
+        if (qq >= R || cs_s[i] == F(0)) continue;
+        const F c = cs_c[i], s = cs_s[i];
+        const F ap = A[pp * R + col], aq = A[qq * R + col];
+        A[pp * R + col] = c * ap - s * aq;
+        A[qq * R + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+    if (!*rotated) break;
+    __syncthreads();
+  }
+  return sweep;
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_mixed(const double* __restrict__ C, int R, int H,
+                                                                double* __restrict__ U, double* __restrict__ eig,
+                                                                int* status) {
+  extern __shared__ __align__(16) double jm[];
+  __shared__ double cd_c[kMixedMaxR / 2 + 1], cd_s[kMixedMaxR / 2 + 1];
+  __shared__ float cf_c[kMixedMaxR / 2 + 1], cf_s[kMixedMaxR / 2 + 1];
+  __shared__ int pr_p[kMixedMaxR / 2 + 1], pr_q[kMixedMaxR / 2 + 1];
+  __shared__ int rotated;
+  __shared__ double anorm;
+  {
+    const size_t b = blockIdx.x;  // batched: one matrix per CTA
+    C += b * R * R;
+    U += b * R * H;
+    eig += b * R;
+  }
+  const int tid = threadIdx.x, nth = blockDim.x, RR = R * R;
+  double* D0 = jm;
+  double* D1 = jm + RR;
+  double* D2 = jm + 2 * RR;
+  double* D3 = jm + 3 * RR;
+  float* Af = reinterpret_cast<float*>(D0);  // FP32 stage: A and V in D0's space
+  float* Vf = Af + RR;
+  for (int i = tid; i < RR; i += nth) {
+    const int r = i / R, c = i % R;
+    Af[i] = (float)(0.5 * (C[i] + C[(size_t)c * R + r]));
+    Vf[i] = (r == c) ? 1.f : 0.f;
+  }
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < R; ++i) m = fmax(m, fabs(C[(size_t)i * R + i]));
+    anorm = m;
+  }
+  __syncthreads();
+  // FP32 stage: off-diagonals down to about single-precision rounding of the largest
+  // diagonal entry (the FP64 stage finishes; below that FP32 sweeps only stir noise)
+  (void)sym_jacobi<float>(Af, Vf, R, 12, 1e-5f, 1e-6f * (float)anorm, cf_c, cf_s, pr_p, pr_q, &rotated);
+  __syncthreads();
+  for (int i = tid; i < RR; i += nth) D1[i] = (double)Vf[i];
+  __syncthreads();
+  // one Newton-Schulz step: V0 = D1 (3 I - D1^T D1) / 2 -> D3
+  smem_mm(D1, true, D1, D2, R);
+  __syncthreads();
+  for (int i = tid; i < RR; i += nth) {
+    const int r = i / R, c = i % R;
+    D2[i] = (r == c ? 1.5 : 0.0) - 0.5 * D2[i];
+  }
+  __syncthreads();
+  smem_mm(D1, false, D2, D3, R);
+  __syncthreads();
+  // A1 = V0^T C V0 (C symmetrised into D0), symmetrised into D1
+  for (int i = tid; i < RR; i += nth) {
+    const int r = i / R, c = i % R;
+    D0[i] = 0.5 * (C[i] + C[(size_t)c * R + r]);
+  }
+  __syncthreads();
+  smem_mm(D0, false, D3, D1, R);
+  __syncthreads();
+  smem_mm(D3, true, D1, D2, R);
+  __syncthreads();
+  for (int i = tid; i < RR; i += nth) {
+    const int r = i / R, c = i % R;
+    D1[i] = 0.5 * (D2[i] + D2[c * R + r]);
+    D0[i] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // FP64 stage on the nearly diagonal A1 (D1) with V1 (D0). Off-diagonals below
+  // 1e-13 of the largest diagonal entry are left: they move an eigenvalue by at
+  // most R x that (about 1e-11 of the largest) and a vector with spectral gap g
+  // by about that / g, while sweeping them to rounding level costs most of the
+  // time for kernels whose many small eigenvalues sit below FP32 resolution.
+  const int sweeps = sym_jacobi<double>(D1, D0, R, kMaxSweeps, 1e-15, 1e-13 * anorm, cd_c, cd_s, pr_p, pr_q,
+                                        &rotated);
+  if (sweeps >= kMaxSweeps && tid == 0) record(status, kDevNoConverge);
+  __syncthreads();
+  smem_mm(D3, false, D0, D2, R);  // eigenvectors V0 V1
+  __syncthreads();
+  // sort by decreasing eigenvalue (stable on index), fix signs, write out
+  for (int i = tid; i < R; i += nth) {
+    const double li = D1[i * R + i];
+    int rank = 0;
+    for (int j = 0; j < R; ++j) {
+      const double lj = D1[j * R + j];
+      if (lj > li || (lj == li && j < i)) ++rank;
+    }
+    eig[rank] = li;
+    if (rank < H) {
+      int imax = 0;
+      double vmax = -1.0;
+      for (int r = 0; r < R; ++r) {
+        const double v = fabs(D2[r * R + i]);
+        if (v > vmax) {
+          vmax = v;
+          imax = r;
+        }
+      }
+      const double sg = D2[imax * R + i] < 0.0 ? -1.0 : 1.0;
+      for (int r = 0; r < R; ++r) U[(size_t)r * H + rank] = sg * D2[r * R + i];
+    }
+  }
+}
+
 }  // namespace
 }  // namespace rsvd
 
@@ -330,14 +524,7 @@ extern "C" int rsvd_build_radial_svd(int R, int Q, const double* w, const void* 
   }
   kernel_reduce<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
   if ((rc = launch_status()) != RSVD_OK) return rc;
-  const size_t need = (size_t)2 * R * R * sizeof(double);
-  const int use_smem = need <= 160 * 1024 ? 1 : 0;
-  const size_t smem = use_smem ? need : 0;
-  if (use_smem &&
-      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return RSVD_ECUDA;
-  jacobi_eig<<<1, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
-  return launch_status();
+  return launch_jacobi(C, A, V, R, H, U, eig, 1, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -660,14 +847,7 @@ extern "C" int rsvd_build_radial_svd_translated(int R, int Q, const double* k, c
   rp.N_B = N_B;
   kernel_reduce_translated<<<(R * R + 255) / 256, 256, 0, st>>>(rp);
   if ((rc = launch_status()) != RSVD_OK) return rc;
-  const size_t need = (size_t)2 * R * R * sizeof(double);
-  const int use_smem = need <= 160 * 1024 ? 1 : 0;
-  const size_t smem = use_smem ? need : 0;
-  if (use_smem &&
-      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return RSVD_ECUDA;
-  jacobi_eig<<<1, kJacobiThreads, smem, st>>>(C, A, V, R, H, U, eig, use_smem, status_word());
-  return launch_status();
+  return launch_jacobi(C, A, V, R, H, U, eig, 1, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -766,14 +946,7 @@ extern "C" int rsvd_build_radial_svd_grouped(int R, int Q, const double* w, cons
   if ((rc = launch_status()) != RSVD_OK) return rc;
   kernel_scale_groups<<<256, 256, 0, st>>>(C, ctf, R, G, Cg);
   if ((rc = launch_status()) != RSVD_OK) return rc;
-  const size_t need = (size_t)2 * R * R * sizeof(double);
-  const int use_smem = need <= 160 * 1024 ? 1 : 0;
-  const size_t smem = use_smem ? need : 0;
-  if (use_smem &&
-      cudaFuncSetAttribute(jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return RSVD_ECUDA;
-  jacobi_eig<<<G, kJacobiThreads, smem, st>>>(Cg, Ag, Vg, R, H, U, eig, use_smem, status_word());
-  if ((rc = launch_status()) != RSVD_OK) return rc;
+  if ((rc = launch_jacobi(Cg, Ag, Vg, R, H, U, eig, G, st)) != RSVD_OK) return rc;
   if (U_targets) {
     kernel_scale_targets<<<256, 256, 0, st>>>(U, ctf, R, H, G, U_targets);
     if ((rc = launch_status()) != RSVD_OK) return rc;
@@ -787,6 +960,13 @@ namespace rsvd {
 // each): U [batch][R][H] leading vectors, eig [batch][R] decreasing.
 RSVD_HIDDEN int launch_jacobi(const double* C, double* A, double* V, int R, int H, double* U, double* eig, int batch,
                               cudaStream_t st) {
+  if (R <= kMixedMaxR) {  // FP32 Jacobi + FP64 polish in shared memory
+    const size_t smem = (size_t)4 * R * R * sizeof(double);
+    if (cudaFuncSetAttribute(jacobi_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return RSVD_ECUDA;
+    jacobi_mixed<<<batch, kJacobiThreads, smem, st>>>(C, R, H, U, eig, status_word());
+    return launch_status();
+  }
   const size_t need = (size_t)2 * R * R * sizeof(double);
   const int use_smem = need <= 160 * 1024 ? 1 : 0;
   const size_t smem = use_smem ? need : 0;
