@@ -938,16 +938,16 @@ def _vol_oracle_chunk(job):
 
 def _vol_flops_per_pair(L, HC, HD, n_beta, Mp):
     """Algorithmic FP32 work per (volume, target) pair of eq. volume_innerproduct_pm
-    for real volumes (X real, Xhat Hermitian in (m1, m2)): Step 1 (8 flops per
-    complex multiply-add over h, on the (m1, m2, l) triples with
-    l >= max(|m1|, |m2|)), Step 1b (4 flops per real x complex term over d), and
-    per interior angle Step 2 on half of the (m1, m2) grid (4 HD flops per
-    entry), the real-output 2-D FFT of the Mp x Mp grid (2.5 N log2 N,
-    N = Mp^2) and the max (1 op per score)."""
+    for real volumes (X real, Xhat Hermitian in (m1, m2), the Step-1 product at -m
+    fixed by the one at m): Step 1 (8 flops per complex multiply-add over h) and
+    Step 1b (4 flops per real x complex term over d) on half of the (m1, m2, l)
+    triples with l >= max(|m1|, |m2|), and per interior angle Step 2 on half of
+    the (m1, m2) grid (4 HD flops per entry), the real-output 2-D FFT of the
+    Mp x Mp grid (2.5 N log2 N, N = Mp^2) and the max (1 op per score)."""
     M = 2 * L + 1
     triples = (L + 1) * (2 * L + 1) * (2 * L + 3) // 3
     per_beta = 4 * HD * (M * M + 1) // 2 + 2.5 * Mp * Mp * math.log2(Mp * Mp) + Mp * Mp
-    return 8 * HC * triples + 4 * HD * triples + n_beta * per_beta
+    return (8 * HC + 4 * HD) * triples / 2 + n_beta * per_beta
 
 
 def _vol_desc(c):
@@ -1023,7 +1023,7 @@ def run_volumes(args):
         P.compress_volume(g.w, U, tgt, out=cB)
         if e:
             e[1].record(stream)
-        P.align_volumes(cA, cB, Vd, tables, Mp, out=(best, arg))
+        P.align_volumes(cA, cB, Vd, tables, Mp, out=(best, arg), real=True)
         if e:
             e[2].record(stream)
 
@@ -1085,7 +1085,7 @@ def run_volumes(args):
 
     def e2e_step():
         P.align_volumes_host(g.w, U, Vd, tables, Mp, vols_h, tgt_h, chunk=chunk, workspace=ws_host,
-                             out=(best_h, arg_h), stream=stream, copy_stream=copy_stream)
+                             out=(best_h, arg_h), real=True, stream=stream, copy_stream=copy_stream)
 
     K2 = max(3, min(K, 10))
     for _ in range(2):
@@ -1104,7 +1104,7 @@ def run_volumes(args):
     flops = N_A * N_B * _vol_flops_per_pair(L, HC, HD, nb, Mp)
     achieved = flops / (align_ms / 1e3) / 1e12
     ept = -(-((M * M + 1) // 2) // 512)
-    kname = f"vol_align_kernel<{Mp},{1 if Mp < 64 else ept}>"
+    kname = f"vol_align_kernel<{Mp},{1 if Mp < 64 else ept},real>"
     out = {
         "metric": "volume·target·rotation scores/sec", "value": world * scores_step * K / (elapsed / 1e3),
         "unit": "scores/s", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": elapsed / K,

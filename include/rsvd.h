@@ -368,6 +368,13 @@ int rsvd_compress_volume(int R, int L, const double* w, const double* U, int HC,
                          void* out, void* stream);
 int rsvd_align_volumes(const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V, int HD,
                        const float* tables, int n_beta, int Mp, float* best, int32_t* arg, void* stream);
+/* Same contract for real volumes and targets (coefficients with
+ * A_l^{-m} = (-1)^{l+m} conj(A_l^m), which compression with real U keeps): the
+ * Step-1 product at -m is then determined by the one at m, and half of Step 1
+ * is skipped. Results agree with rsvd_align_volumes up to rounding on such
+ * inputs; other inputs give the wrong scores. */
+int rsvd_align_volumes_real(const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V, int HD,
+                            const float* tables, int n_beta, int Mp, float* best, int32_t* arg, void* stream);
 
 /* ------------------------------------------------------------------------
  * Host-input pipeline: rsvd_compress (templates, then images) and
@@ -418,15 +425,16 @@ int rsvd_align_grouped(int R, int Q, const double* k, const double* w, const dou
  * tables on the device as for rsvd_compress_volume and rsvd_align_volumes;
  * best, arg host [N_A][N_B]. The targets are copied and compressed first, then
  * the volumes in chunks of `chunk` on copy_stream (a stream other than
- * `stream`), the copy of chunk c + 1 overlapping the work on chunk c. Returns
+ * `stream`), the copy of chunk c + 1 overlapping the work on chunk c;
+ * real_volumes != 0 aligns with rsvd_align_volumes_real. Returns
  * after enqueueing; `stream` waits for the last copy back. workspace >=
  * rsvd_align_volumes_host_workspace_bytes(R, L, H_C, N_B, chunk), device,
  * 256-byte aligned. */
 size_t rsvd_align_volumes_host_workspace_bytes(int R, int L, int HC, int N_B, int chunk);
 int rsvd_align_volumes_host(int R, int L, const double* w, const double* U, int HC, const double* V, int HD,
                             const float* tables, int n_beta, int Mp, const void* volumes, int N_A, const void* targets,
-                            int N_B, float* best, int32_t* arg, int chunk, void* workspace, size_t workspace_bytes,
-                            void* stream, void* copy_stream);
+                            int N_B, int real_volumes, float* best, int32_t* arg, int chunk, void* workspace,
+                            size_t workspace_bytes, void* stream, void* copy_stream);
 
 /* Same contract as rsvd_align_best, always on the generic per-pair kernel
  * (one CTA per (image, template), all T translations, any supported Q and H).

@@ -62,8 +62,8 @@ SIGNATURES = {
                                    c_void_p, c_void_p, c_size_t, c_void_pp, c_int]),
     "rsvd_align_volumes_host_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "rsvd_align_volumes_host": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
-                                        c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p,
-                                        c_size_t, c_void_p, c_void_p]),
+                                        c_int, c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_int,
+                                        c_void_p, c_size_t, c_void_p, c_void_p]),
     "rsvd_align_host_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
     "rsvd_align_best_host": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_void_p, c_int,
                                      c_double_p, c_int, c_void_p, c_int, c_int, c_float, c_void_p, c_void_p,
@@ -75,6 +75,8 @@ SIGNATURES = {
     "rsvd_compress_volume": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     "rsvd_align_volumes": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int,
                                    c_int, c_void_p, c_void_p, c_void_p]),
+    "rsvd_align_volumes_real": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p,
+                                        c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "rsvd_build_grouped_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
     "rsvd_build_radial_svd_grouped": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                               c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

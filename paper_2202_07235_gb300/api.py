@@ -239,8 +239,9 @@ def compress_volume(w, U: torch.Tensor, volumes: torch.Tensor, out: torch.Tensor
 
 
 def align_volumes(cA: torch.Tensor, cB: torch.Tensor, V: torch.Tensor, tables: torch.Tensor, Mp: int, out=None,
-                  stream=None):
-    """best float32 [N_A, N_B], arg int32 (b*Mp^2 + a*Mp + c)."""
+                  real: bool = False, stream=None):
+    """best float32 [N_A, N_B], arg int32 (b*Mp^2 + a*Mp + c). real=True for real
+    volumes and targets (rsvd_align_volumes_real: half of Step 1)."""
     _require_cuda(cA, torch.complex64, "cA")
     _require_cuda(cB, torch.complex64, "cB")
     _require_cuda(V, torch.float64, "V")
@@ -253,8 +254,9 @@ def align_volumes(cA: torch.Tensor, cB: torch.Tensor, V: torch.Tensor, tables: t
         arg = torch.empty((N_A, N_B), dtype=torch.int32, device=cA.device)
     else:
         best, arg = out
-    check(lib().rsvd_align_volumes(_ptr(cA), N_A, _ptr(cB), N_B, HC, L1 - 1, _ptr(V), HD, _ptr(tables), n_beta, Mp,
-                                   _ptr(best), _ptr(arg), _stream(stream)), "rsvd_align_volumes")
+    fn = lib().rsvd_align_volumes_real if real else lib().rsvd_align_volumes
+    check(fn(_ptr(cA), N_A, _ptr(cB), N_B, HC, L1 - 1, _ptr(V), HD, _ptr(tables), n_beta, Mp, _ptr(best), _ptr(arg),
+             _stream(stream)), "rsvd_align_volumes")
     return best, arg
 
 
@@ -319,8 +321,8 @@ def align_best_host(k, w, U: torch.Tensor, images: torch.Tensor, templates: torc
 
 
 def align_volumes_host(w, U: torch.Tensor, V: torch.Tensor, tables: torch.Tensor, Mp: int, volumes: torch.Tensor,
-                       targets: torch.Tensor, chunk: int | None = None, workspace=None, out=None, stream=None,
-                       copy_stream=None):
+                       targets: torch.Tensor, chunk: int | None = None, workspace=None, out=None, real: bool = False,
+                       stream=None, copy_stream=None):
     """rsvd_align_volumes_host: volumes complex64 [N_A, R, L+1, 2L+1] and targets
     [N_B, ...] in host memory (pinned for overlap); returns host (best, arg) after
     synchronising `stream`."""
@@ -347,7 +349,7 @@ def align_volumes_host(w, U: torch.Tensor, V: torch.Tensor, tables: torch.Tensor
     s = stream if stream is not None else torch.cuda.current_stream()
     cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=U.device)
     check(lib().rsvd_align_volumes_host(R, L1 - 1, wp, _ptr(U), HC, _ptr(V), HD, _ptr(tables), tables.shape[0], Mp,
-                                        _ptr(volumes), N_A, _ptr(targets), N_B, _ptr(best), _ptr(arg), chunk,
+                                        _ptr(volumes), N_A, _ptr(targets), N_B, int(real), _ptr(best), _ptr(arg), chunk,
                                         _ptr(workspace), workspace.numel(), int(s.cuda_stream), int(cs.cuda_stream)),
           "rsvd_align_volumes_host")
     s.synchronize()

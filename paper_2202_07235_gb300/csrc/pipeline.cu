@@ -271,8 +271,9 @@ extern "C" size_t rsvd_align_volumes_host_workspace_bytes(int R, int L, int HC, 
 
 extern "C" int rsvd_align_volumes_host(int R, int L, const double* w, const double* U, int HC, const double* V, int HD,
                                        const float* tables, int n_beta, int Mp, const void* volumes, int N_A,
-                                       const void* targets, int N_B, float* best, int32_t* arg, int chunk,
-                                       void* workspace, size_t workspace_bytes, void* stream, void* copy_stream) {
+                                       const void* targets, int N_B, int real_volumes, float* best, int32_t* arg,
+                                       int chunk, void* workspace, size_t workspace_bytes, void* stream,
+                                       void* copy_stream) {
   if (!w || !U || !V || !tables || !volumes || !targets || !best || !arg || R <= 0 || L < 1 || HC <= 0 || HD <= 0 ||
       n_beta <= 0 || N_A <= 0 || N_B <= 0 || chunk <= 0)
     return RSVD_EINVAL;
@@ -322,7 +323,8 @@ extern "C" int rsvd_align_volumes_host(int R, int L, const double* w, const doub
     if ((rc = rsvd_compress_volume(R, L, w, U, HC, vol[b], n, cA, stream)) != RSVD_OK) return rc;
     if (cudaEventRecord(ev_used[b], st) != cudaSuccess) return RSVD_ECUDA;
     if (c >= 2 && cudaStreamWaitEvent(st, ev_back[b], 0) != cudaSuccess) return RSVD_ECUDA;
-    rc = rsvd_align_volumes(cA, n, cB, N_B, HC, L, V, HD, tables, n_beta, Mp, best_d[b], arg_d[b], stream);
+    rc = (real_volumes ? rsvd_align_volumes_real : rsvd_align_volumes)(cA, n, cB, N_B, HC, L, V, HD, tables, n_beta,
+                                                                        Mp, best_d[b], arg_d[b], stream);
     if (rc != RSVD_OK) return rc;
     if (cudaEventRecord(ev_done[b], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev_done[b], 0) != cudaSuccess)
       return RSVD_ECUDA;

@@ -19,6 +19,8 @@
 //   running max / argmax over (beta, alpha, gamma).
 #include <math.h>
 
+#include <type_traits>
+
 #include "align_common.cuh"
 
 namespace rsvd {
@@ -304,7 +306,10 @@ __device__ __forceinline__ void best8(const float (&v)[8], int base, int step, f
 //    [64][65] grid (line = thread mod 64); the next pair's table entries are
 //    fetched asynchronously into per-thread slots during the transform.
 //  Mp = 16, 32: radix-2 passes in shared memory on bit-reversed input.
-template <int Mp, int EPT>
+// kReal: the volumes and targets are real (A_l^{-m} = (-1)^{l+m} conj A_l^m), so
+// the mirror product equals (-1)^{m1-m2} conj of the direct one and the
+// Hermitian part of Step 1b is the direct accumulation: half the Step-1 work.
+template <int Mp, int EPT, bool kReal>
 __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_constant__ VolAlignParams p) {
   extern __shared__ __align__(16) unsigned char vsm[];
   const int L = p.L, M = 2 * L + 1, LM = (L + 1) * M, HC = p.HC, MM = M * M, Mh = (MM + 1) / 2;
@@ -357,13 +362,16 @@ __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_c
         const float2* ah = sa + l * M;
         const float2* bh = sb + l * M;
         for (int h = 0; h < HC; ++h, ah += hstride, bh += hstride) {
-          const float2 a = ah[i1], b = bh[i2], a2 = ah[2 * L - i1], b2 = bh[2 * L - i2];
+          const float2 a = ah[i1], b = bh[i2];
           x.x = fmaf(a.x, b.x, fmaf(a.y, b.y, x.x));
           x.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, x.y));
-          y.x = fmaf(a2.x, b2.x, fmaf(a2.y, b2.y, y.x));
-          y.y = fmaf(a2.x, b2.y, fmaf(-a2.y, b2.x, y.y));
+          if constexpr (!kReal) {
+            const float2 a2 = ah[2 * L - i1], b2 = bh[2 * L - i2];
+            y.x = fmaf(a2.x, b2.x, fmaf(a2.y, b2.y, y.x));
+            y.y = fmaf(a2.x, b2.y, fmaf(-a2.y, b2.x, y.y));
+          }
         }
-        const float2 xh = make_float2(fmaf(0.5f, x.x, s * y.x), fmaf(0.5f, x.y, -s * y.y));
+        const float2 xh = kReal ? x : make_float2(fmaf(0.5f, x.x, s * y.x), fmaf(0.5f, x.y, -s * y.y));
         const float4 v0 = *reinterpret_cast<const float4*>(Vs + l * kVolMaxHD);
         const float4 v1 = *reinterpret_cast<const float4*>(Vs + l * kVolMaxHD + 4);
         const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
@@ -689,10 +697,10 @@ extern "C" int rsvd_compress_volume(int R, int L, const double* w, const double*
   return launch_status();
 }
 
-extern "C" int rsvd_align_volumes(const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V,
-                                  int HD, const float* tables, int n_beta, int Mp, float* best, int32_t* arg,
-                                  void* stream) {
-  using namespace rsvd;
+namespace rsvd {
+namespace {
+int align_volumes_impl(bool real, const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V,
+                       int HD, const float* tables, int n_beta, int Mp, float* best, int32_t* arg, void* stream) {
   if (!cA || !cB || !V || !tables || !best || !arg || N_A <= 0 || N_B <= 0 || HC <= 0 || L < 1 || HD <= 0 ||
       n_beta <= 0)
     return RSVD_EINVAL;
@@ -724,11 +732,29 @@ extern "C" int rsvd_align_volumes(const void* cA, int N_A, const void* cB, int N
     kern<<<(unsigned)((long long)N_A * N_B), kAlignThreads, smem, st>>>(ap);
     return launch_status();
   };
-  if (Mp == 16) return go(vol_align_kernel<16, 1>);
-  if (Mp == 32) return go(vol_align_kernel<32, 1>);
-  if (ept <= 1) return go(vol_align_kernel<64, 1>);
-  if (ept <= 2) return go(vol_align_kernel<64, 2>);
-  if (ept <= 3) return go(vol_align_kernel<64, 3>);
-  if (ept <= 4) return go(vol_align_kernel<64, 4>);
-  return RSVD_EUNSUPPORTED;
+  auto pick = [&](auto real_tag) -> int {
+    constexpr bool R_ = decltype(real_tag)::value;
+    if (Mp == 16) return go(vol_align_kernel<16, 1, R_>);
+    if (Mp == 32) return go(vol_align_kernel<32, 1, R_>);
+    if (ept <= 1) return go(vol_align_kernel<64, 1, R_>);
+    if (ept <= 2) return go(vol_align_kernel<64, 2, R_>);
+    if (ept <= 3) return go(vol_align_kernel<64, 3, R_>);
+    if (ept <= 4) return go(vol_align_kernel<64, 4, R_>);
+    return (int)RSVD_EUNSUPPORTED;
+  };
+  return real ? pick(std::true_type{}) : pick(std::false_type{});
+}
+}  // namespace
+}  // namespace rsvd
+
+extern "C" int rsvd_align_volumes(const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V,
+                                  int HD, const float* tables, int n_beta, int Mp, float* best, int32_t* arg,
+                                  void* stream) {
+  return rsvd::align_volumes_impl(false, cA, N_A, cB, N_B, HC, L, V, HD, tables, n_beta, Mp, best, arg, stream);
+}
+
+extern "C" int rsvd_align_volumes_real(const void* cA, int N_A, const void* cB, int N_B, int HC, int L,
+                                       const double* V, int HD, const float* tables, int n_beta, int Mp, float* best,
+                                       int32_t* arg, void* stream) {
+  return rsvd::align_volumes_impl(true, cA, N_A, cB, N_B, HC, L, V, HD, tables, n_beta, Mp, best, arg, stream);
 }

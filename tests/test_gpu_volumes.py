@@ -158,6 +158,38 @@ def test_volume_host_pipeline_equals_device_path():
     bd, ad = P.align_volumes(cA, cB, Vd, T, 32)
     bh, ah = P.align_volumes_host(g.w, U, Vd, T, 32, torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(),
                                   chunk=5)
+    bhr, ahr = P.align_volumes_host(g.w, U, Vd, T, 32, torch.from_numpy(A).pin_memory(),
+                                    torch.from_numpy(B).pin_memory(), chunk=5, real=True)
+    brd, ard = P.align_volumes(cA, cB, Vd, T, 32, real=True)
+    P.status()
+    assert np.array_equal(bhr.numpy(), brd.cpu().numpy()) and np.array_equal(ahr.numpy(), ard.cpu().numpy())
     P.status()
     assert np.array_equal(bh.numpy(), bd.cpu().numpy())
     assert np.array_equal(ah.numpy(), ad.cpu().numpy())
+
+
+@pytest.mark.parametrize("L,R,HC,HD,n_beta,Mp", [(8, 8, 5, 6, 9, 32), (24, 12, 8, 8, 5, 64), (7, 6, 6, 8, 6, 16)])
+def test_real_volume_path_matches_general_path_and_oracle(L, R, HC, HD, n_beta, Mp):
+    """Synthetic volumes are real (A_l^{-m} = (-1)^{l+m} conj A_l^m): the shortcut path
+    agrees with the general one and with the oracle."""
+    wl, A, B = _wl(L=L, R=R, N_B=2, N_A=4, n_beta=n_beta, Mp=Mp, seed=40 + L)
+    g = wl.grid
+    Bd, Ad = B.astype(np.complex128), A.astype(np.complex128)
+    Ur, _ = V.volume_principal(V.volume_radial_kernel(Bd, g.w), HC)
+    Vr, _ = V.volume_principal(V.volume_degree_kernel(Bd, g.w), HD)
+    Ut, Vt = torch.from_numpy(Ur).to(DEV), torch.from_numpy(Vr).to(DEV)
+    cA = P.compress_volume(g.w, Ut, torch.from_numpy(A).to(DEV))
+    cB = P.compress_volume(g.w, Ut, torch.from_numpy(B).to(DEV))
+    T = P.volume_tables(Vt, wl.betas)
+    bg, ag = P.align_volumes(cA, cB, Vt, T, Mp)
+    br, ar = P.align_volumes(cA, cB, Vt, T, Mp, real=True)
+    P.status()
+    X = V.volume_scores_compressed(V.compress_volume(Ad, Ur, g.w), V.compress_volume(Bd, Ur, g.w), Vr, wl.betas, Mp)
+    rb, ra = V.volume_align_best(X)
+    flat = X.reshape(4, 2, -1)
+    scale = np.abs(flat).max(axis=-1)
+    br, ar, bg = br.cpu().numpy(), ar.cpu().numpy(), bg.cpu().numpy()
+    assert np.all(np.abs(br - bg) <= RTOL * scale)
+    assert np.all(np.abs(br - rb) <= RTOL * scale)
+    at = np.take_along_axis(flat, ar[..., None].astype(np.int64), axis=-1)[..., 0]
+    assert np.all((ar == ra) | (at >= rb - RTOL * scale))

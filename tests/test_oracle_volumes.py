@@ -115,3 +115,19 @@ def test_wigner_d_mirror_symmetry():
             d = V.wigner_d(l, beta)
             sign = (-1.0) ** (m[:, None] - m[None, :])
             assert np.allclose(d[::-1, ::-1], sign * d, atol=1e-13)
+
+
+def test_real_volumes_mirror_product():
+    """For real volumes the Step-1 product at -m is (-1)^{m1-m2} conj of the one at
+    m, so the Hermitian part of Step 1b is the direct product (the real-volume
+    shortcut)."""
+    wl = _small(seed=8)
+    g = wl.grid
+    L = g.L
+    U = np.linalg.qr(np.random.default_rng(1).standard_normal((g.R, g.R)))[0][:, :3]
+    a = V.compress_volume(wl.volumes, U, g.w)
+    b = V.compress_volume(wl.targets, U, g.w)
+    x = np.einsum("nhlx,jhly->njlxy", np.conj(a), b)
+    m = np.arange(-L, L + 1)
+    s = (-1.0) ** (m[:, None] - m[None, :])
+    assert np.allclose(s * np.conj(x[..., ::-1, ::-1]), x, rtol=0, atol=1e-12 * np.abs(x).max())
