@@ -185,19 +185,56 @@ def _peaks():
         return {}
 
 
+def _form_roofline(P, fp, N_A, N_B, T, H, Q, align_ms, sm_count):
+    """Roofline of tc_align_kernel for one operand form: the slowest of three
+    floors, the Step-1 contraction at the tensor peak (8 flops per complex
+    multiply-add over the Q/2+1 frequencies, per operand term), the transform
+    over q and the reduction at the FP32 ALU peak, and the compressed operands
+    and per-pair outputs at the HBM peak; with the tensor pipe's own figures
+    and the MMA-instruction floor."""
+    pairs = N_A * T * N_B
+    terms = 3 if fp == "bf16x3" else 1
+    gemm = pairs * 8 * H * (Q // 2 + 1) * terms
+    fft = pairs * (2.5 * Q * math.log2(Q) + 2 * Q)
+    nbytes = P.compressed_bytes(N_A, T, H, Q, fp) + P.compressed_bytes(N_B, 1, H, Q, fp) + N_A * N_B * 8
+    pk = _peaks()
+    peak_t = pk.get("bf16_tflops_sustained") or 1700.0
+    peak_a = sm_count * 128 * 2 * 2.07e9 / 1e12
+    peak_h = pk.get("hbm_gbs") or 6800.0
+    floors = {"tensor": gemm / (peak_t * 1e12) * 1e3, "alu": fft / (peak_a * 1e12) * 1e3,
+              "hbm": nbytes / (peak_h * 1e9) * 1e3}
+    bound = max(floors, key=floors.get)
+    # MMA count: tiles of 128 rows (whole images) x 512/Q templates, 32 slot groups,
+    # K = 2 Hp g per group in steps of 16
+    g = Q // 64
+    Hp = -(-H // (8 // g)) * (8 // g)
+    tiles = (-(-N_A // (128 // T))) * (-(-N_B // (512 // Q)))
+    mma = tiles * 32 * (2 * Hp * g // 16) * terms
+    # instruction floor: 39.4 cycles per M=128 N=16 K=16 MMA issued back to back
+    # (measured in isolation on this GPU), at the max SM clock
+    floor_ms = mma / sm_count * 39.4 / 2.07e9 * 1e3
+    sec = align_ms / 1e3
+    work, peak, unit = {"hbm": (nbytes / 1e9, peak_h, "GB/s"), "alu": (fft / 1e12, peak_a, "TFLOP/s"),
+                        "tensor": (gemm / 1e12, peak_t, "TFLOP/s")}[bound]
+    return {"bound": bound, "kernel": f"tc_align_kernel<{Q},false>", "achieved": round(work / sec, 2),
+            "peak": round(peak, 2), "unit": unit, "frac": round(floors[bound] / align_ms, 4),
+            "floors_ms": {k: round(v, 3) for k, v in floors.items()},
+            "peak_basis": (f"transform + reduction flops; {sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
+                           if bound == "alu" else "of measured"),
+            "tensor": {"achieved": round(gemm / sec / 1e12, 2), "peak": peak_t, "unit": "TFLOP/s",
+                       "frac": round(gemm / sec / 1e12 / peak_t, 4),
+                       "peak_basis": "measured bf16 dense GEMM, sustained (of measured)",
+                       "mma_per_launch": mma, "mma_floor_ms": round(floor_ms, 3),
+                       "mma_floor_frac": round(floor_ms / align_ms, 4)}}
+
+
 def _measure_forms(P, torch, grid, U, imgs, tmpl, deltas, cfg, T, K2, scores_step, dev):
     """Step time (compress + align_best) of each tensor-core operand form, with
-    the tensor roofline of the scoring kernel (the Step-1 contraction's flops
-    against the measured bf16 peak) and its MMA-instruction floor."""
+    the scoring kernel's roofline (the slowest of its tensor, FP32-ALU and HBM
+    floors), its tensor-pipe figures and its MMA-instruction floor."""
     N_A, N_B, Q, H = cfg["N_A"], cfg["N_B"], cfg["Q"], cfg["H"]
     stream = torch.cuda.current_stream()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    g = Q // 64
-    step = 8 // g
-    Hp = -(-H // step) * step
-    Kc = 2 * Hp * g
-    ipt = 128 // T
-    tiles = (-(-N_A // ipt)) * (-(-N_B // (512 // Q)))
     res = {}
     for fp in ("bf16", "fp16", "bf16x3"):
         try:
@@ -227,25 +264,9 @@ def _measure_forms(P, torch, grid, U, imgs, tmpl, deltas, cfg, T, K2, scores_ste
             P.status()
             step_ms = sum(e[0].elapsed_time(e[2]) for e in ev) / K2
             align_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K2
-            pairs = N_A * T * N_B
-            terms = 3 if fp == "bf16x3" else 1
-            # Step-1 contraction on the tensor cores: 8 flops per complex multiply-add
-            # over the Q/2+1 frequencies, per operand term
-            flops = pairs * 8 * H * (Q // 2 + 1) * terms
-            achieved = flops / (align_ms / 1e3) / 1e12
-            peak = _peaks().get("bf16_tflops_sustained") or 1700.0
-            mma = tiles * 32 * (Kc // 16) * terms
-            # instruction floor: 39.4 cycles per M=128 N=16 K=16 MMA issued back to back
-            # (measured in isolation on this GPU), at the max SM clock
-            floor_ms = mma / sm_count * 39.4 / 2.07e9 * 1e3
             rep = {"value": scores_step / (step_ms / 1e3), "unit": UNIT, "ms_per_step": step_ms,
                    "align_ms": align_ms, "compress_ms": step_ms - align_ms,
-                   "roofline": {"bound": "tensor", "kernel": f"tc_align_kernel<{Q},false>",
-                                "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                                "frac": round(achieved / peak, 4),
-                                "peak_basis": "measured bf16 dense GEMM, sustained (of measured)",
-                                "mma_per_launch": mma, "mma_floor_ms": round(floor_ms, 3),
-                                "mma_floor_frac": round(floor_ms / align_ms, 4)}}
+                   "roofline": _form_roofline(P, fp, N_A, N_B, T, H, Q, align_ms, sm_count)}
             res[fp] = {"report": rep, "best": bf, "arg": af}
             del cAf, cBf
         except Exception as e:  # a form outside its size limits
@@ -409,16 +430,20 @@ def run_ours(args):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
     kname = f"ws_align_kernel<{Q // 2},{12 if H <= 12 else 16}>" if (Q == 256 and H <= 16) else "fused_align_kernel"
-    roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
-                "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": _load_traffic(kname + "@" + args.config) if args.n_images == 0 else None,
-                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
-                "align_ms": round(align_avg_ms, 3), "compress_ms": round(sum(compress_ms) / K, 3)}
+    if prec == "fp32":
+        roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
+                    "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": _load_traffic(kname + "@" + args.config) if args.n_images == 0 else None,
+                    "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)"}
+    else:
+        roofline = _form_roofline(P, prec, N_A, N_B, T, H, Q, align_avg_ms, sm_count)
+        roofline["traffic"] = None
+    roofline.update(align_ms=round(align_avg_ms, 3), compress_ms=round(sum(compress_ms) / K, 3))
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
+        "dtype": "f32" if prec == "fp32" else prec, "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
         "config": {"workload": _workload_desc(cfg), "N_A_per_gpu": N_A, "N_B": N_B, "T": T, "Q": Q, "R": R, "H": H,
                    "N": cfg["N"], "snr": cfg["snr"], "parallelism": f"dp{world} (images sharded, templates replicated)",
                    "l2": "inputs larger than L2 (polar images %.2f GB/GPU), no flush" % (imgs.numel() * 8 / 1e9),
