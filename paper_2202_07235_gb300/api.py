@@ -49,6 +49,35 @@ def _require_cuda(t: torch.Tensor, dtype, name: str):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _require_dev_bytes(t: torch.Tensor, nbytes: int, name: str):
+    """A contiguous CUDA tensor of at least `nbytes` bytes (the C ABI takes plain
+    pointers, so the sizes are checked here, before any launch)."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError(f"{name} holds {have} bytes, {nbytes} needed")
+
+
+def _require_out(t: torch.Tensor, shape, dtype, name: str, cuda: bool = True):
+    (_require_cuda if cuda else _require_host)(t, dtype, name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _require_operands(cA, N_A: int, T: int, cB, N_B: int, H: int, Q: int, precision: int):
+    _require_dev_bytes(cA, compressed_bytes(N_A, T, H, Q, precision), "cA")
+    _require_dev_bytes(cB, compressed_bytes(N_B, 1, H, Q, precision), "cB")
+
+
+def _require_U(U: torch.Tensor, R: int, name: str = "U"):
+    _require_cuda(U, torch.float64, name)
+    if U.dim() != 2 or U.shape[0] != R:
+        raise ValueError(f"{name} must be float64 [{R}, H], got {tuple(U.shape)}")
+
+
 def build_workspace_bytes(R: int, Q: int, N_B: int) -> int:
     return int(lib().rsvd_build_workspace_bytes(R, Q, N_B))
 
@@ -153,6 +182,10 @@ def align_grouped(k, w, images: torch.Tensor, offsets, templates: torch.Tensor, 
     _require_cuda(U_targets, torch.float64, "U_targets")
     N_A, R, Q = images.shape
     N_B = templates.shape[0]
+    if tuple(templates.shape[1:]) != (R, Q):
+        raise ValueError("templates must be complex64 [N_B, R, Q] like the images")
+    if U.dim() != 3 or U.shape[1] != R or tuple(U_targets.shape) != tuple(U.shape):
+        raise ValueError("U and U_targets must be float64 [G, R, H]")
     G, _, H = U.shape
     ka, kp = _host_f64(k)
     wa, wp = _host_f64(w)
@@ -223,8 +256,8 @@ def compress_volume(w, U: torch.Tensor, volumes: torch.Tensor, out: torch.Tensor
                     stream=None) -> torch.Tensor:
     """Principal-volume-shells, complex64 [N, HC, L+1, 2L+1]."""
     _require_cuda(volumes, torch.complex64, "volumes")
-    _require_cuda(U, torch.float64, "U")
     N, R, L1, M = volumes.shape
+    _require_U(U, R)
     HC = U.shape[1]
     wa, wp = _host_f64(w)
     if out is None:
@@ -246,14 +279,22 @@ def align_volumes(cA: torch.Tensor, cB: torch.Tensor, V: torch.Tensor, tables: t
     _require_cuda(cB, torch.complex64, "cB")
     _require_cuda(V, torch.float64, "V")
     _require_cuda(tables, torch.float32, "tables")
-    N_A, HC, L1, _ = cA.shape
+    N_A, HC, L1, M = cA.shape
     N_B = cB.shape[0]
+    if tuple(cB.shape[1:]) != (HC, L1, M) or M != 2 * L1 - 1:
+        raise ValueError("cA and cB must be [N, HC, L+1, 2L+1] with the same HC and L")
+    if V.dim() != 2 or V.shape[0] != L1:
+        raise ValueError("V must be float64 [L+1, HD]")
     n_beta, HD = tables.shape[0], V.shape[1]
+    if tuple(tables.shape[1:]) != (M, M, VOL_TABLE_D):
+        raise ValueError(f"tables must be float32 [n_beta, {M}, {M}, {VOL_TABLE_D}]")
     if out is None:
         best = torch.empty((N_A, N_B), dtype=torch.float32, device=cA.device)
         arg = torch.empty((N_A, N_B), dtype=torch.int32, device=cA.device)
     else:
         best, arg = out
+        _require_out(best, (N_A, N_B), torch.float32, "best")
+        _require_out(arg, (N_A, N_B), torch.int32, "arg")
     fn = lib().rsvd_align_volumes_real if real else lib().rsvd_align_volumes
     check(fn(_ptr(cA), N_A, _ptr(cB), N_B, HC, L1 - 1, _ptr(V), HD, _ptr(tables), n_beta, Mp, _ptr(best), _ptr(arg),
              _stream(stream)), "rsvd_align_volumes")
@@ -283,8 +324,10 @@ def align_best_host(k, w, U: torch.Tensor, images: torch.Tensor, templates: torc
     precision = _prec(precision)
     _require_host(images, torch.complex64, "images")
     _require_host(templates, torch.complex64, "templates")
-    _require_cuda(U, torch.float64, "U")
     N_A, R, Q = images.shape
+    if tuple(templates.shape[1:]) != (R, Q):
+        raise ValueError("templates must be complex64 [N_B, R, Q] like the images")
+    _require_U(U, R)
     N_B = templates.shape[0]
     H = U.shape[1]
     ka, kp = _host_f64(k)
@@ -309,6 +352,12 @@ def align_best_host(k, w, U: torch.Tensor, images: torch.Tensor, templates: torc
         lse = torch.empty((N_A, N_B), dtype=torch.float32).pin_memory() if want_lse else None
     else:
         best, arg, lse = out
+        _require_out(best, (N_A, N_B), torch.float32, "best", cuda=False)
+        _require_out(arg, (N_A, N_B), torch.int32, "arg", cuda=False)
+        if want_lse != (lse is not None):
+            raise ValueError("out must hold an lse buffer exactly when want_lse")
+        if lse is not None:
+            _require_out(lse, (N_A, N_B), torch.float32, "lse", cuda=False)
     s = stream if stream is not None else torch.cuda.current_stream()
     cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=U.device)
     check(lib().rsvd_align_best_host(R, Q, kp, wp, _ptr(U), H, _ptr(images), N_A, dp, T, _ptr(templates), N_B,
@@ -332,6 +381,13 @@ def align_volumes_host(w, U: torch.Tensor, V: torch.Tensor, tables: torch.Tensor
     _require_cuda(V, torch.float64, "V")
     _require_cuda(tables, torch.float32, "tables")
     N_A, R, L1, M = volumes.shape
+    if tuple(targets.shape[1:]) != (R, L1, M):
+        raise ValueError("targets must be complex64 [N_B, R, L+1, 2L+1] like the volumes")
+    _require_U(U, R)
+    if V.dim() != 2 or V.shape[0] != L1:
+        raise ValueError("V must be float64 [L+1, HD]")
+    if tuple(tables.shape[1:]) != (M, M, VOL_TABLE_D):
+        raise ValueError(f"tables must be float32 [n_beta, {M}, {M}, {VOL_TABLE_D}]")
     N_B = targets.shape[0]
     HC, HD = U.shape[1], V.shape[1]
     wa, wp = _host_f64(w)
@@ -346,6 +402,8 @@ def align_volumes_host(w, U: torch.Tensor, V: torch.Tensor, tables: torch.Tensor
         arg = torch.empty((N_A, N_B), dtype=torch.int32).pin_memory()
     else:
         best, arg = out
+        _require_out(best, (N_A, N_B), torch.float32, "best", cuda=False)
+        _require_out(arg, (N_A, N_B), torch.int32, "arg", cuda=False)
     s = stream if stream is not None else torch.cuda.current_stream()
     cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=U.device)
     check(lib().rsvd_align_volumes_host(R, L1 - 1, wp, _ptr(U), HC, _ptr(V), HD, _ptr(tables), tables.shape[0], Mp,
@@ -375,8 +433,8 @@ def compress(k, w, U: torch.Tensor, polar: torch.Tensor, deltas=None, precision:
     tensor (layout in include/rsvd.h)."""
     precision = _prec(precision)
     _require_cuda(polar, torch.complex64, "polar")
-    _require_cuda(U, torch.float64, "U")
     N, R, Q = polar.shape
+    _require_U(U, R)
     H = U.shape[1]
     ka, kp = _host_f64(k)
     wa, wp = _host_f64(w)
@@ -390,6 +448,7 @@ def compress(k, w, U: torch.Tensor, polar: torch.Tensor, deltas=None, precision:
             out = torch.empty((N * T, H, Q // 2, 2), dtype=torch.float32, device=polar.device)
         else:
             out = _operand_buffer(N, T, H, Q, precision, polar.device)
+    _require_dev_bytes(out, compressed_bytes(N, T, H, Q, precision), "out")
     check(lib().rsvd_compress(R, Q, kp, wp, _ptr(U), H, _ptr(polar), N, dp, T, precision, _ptr(out),
                               _stream(stream)), "rsvd_compress")
     return out
@@ -401,8 +460,10 @@ def pack(c32: torch.Tensor, N: int, T: int, H: int, Q: int, precision, out: torc
     `precision` (byte tensor), rounded to nearest."""
     precision = _prec(precision)
     _require_cuda(c32, torch.float32, "c32")
+    _require_dev_bytes(c32, compressed_bytes(N, T, H, Q, FP32), "c32")
     if out is None:
         out = _operand_buffer(N, T, H, Q, precision, c32.device)
+    _require_dev_bytes(out, compressed_bytes(N, T, H, Q, precision), "out")
     check(lib().rsvd_pack(_ptr(c32), N, T, H, Q, precision, _ptr(out), _stream(stream)), "rsvd_pack")
     return out
 
@@ -411,6 +472,7 @@ def align_scores(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int,
                  precision=FP32, stream=None) -> torch.Tensor:
     """Full landscape X float32 [N_A, T, N_B, Q]."""
     precision = _prec(precision)
+    _require_operands(cA, N_A, T, cB, N_B, H, Q, precision)
     X = torch.empty((N_A, T, N_B, Q), dtype=torch.float32, device=cA.device)
     check(lib().rsvd_align_scores(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, _ptr(X), _stream(stream)),
           "rsvd_align_scores")
@@ -422,6 +484,7 @@ def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H
                pairwise: bool = False):
     """best float32 [N_A, N_B], arg int32 [N_A, N_B] (t*Q+m), lse float32 or None."""
     precision = _prec(precision)
+    _require_operands(cA, N_A, T, cB, N_B, H, Q, precision)
     dev = cA.device
     if out is None:
         best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
@@ -429,6 +492,10 @@ def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H
         lse = torch.empty((N_A, N_B), dtype=torch.float32, device=dev) if want_lse else None
     else:
         best, arg, lse = out
+        _require_out(best, (N_A, N_B), torch.float32, "best")
+        _require_out(arg, (N_A, N_B), torch.int32, "arg")
+        if lse is not None:
+            _require_out(lse, (N_A, N_B), torch.float32, "lse")
     fn = lib().rsvd_align_best_pairwise if pairwise else lib().rsvd_align_best
     check(fn(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, float(inv_sigma2), _ptr(best), _ptr(arg),
              _ptr(lse) if lse is not None else None, _stream(stream)), "rsvd_align_best")
@@ -438,6 +505,7 @@ def align_best(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H
 def align_scores_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int, P: int,
                       stream=None) -> torch.Tensor:
     """Landscape on the P-times finer rotation grid, float32 [N_A, T, N_B, P*Q]."""
+    _require_operands(cA, N_A, T, cB, N_B, H, Q, FP32)
     X = torch.empty((N_A, T, N_B, P * Q), dtype=torch.float32, device=cA.device)
     check(lib().rsvd_align_scores_fine(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, P, FP32, _ptr(X), _stream(stream)),
           "rsvd_align_scores_fine")
@@ -451,6 +519,7 @@ def align_best_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: i
     method "shifted": P passes of the fused kernels against templates rotated by
     p/P of a grid step (rsvd_align_best_fine_shifted); "pair": the generic
     per-pair kernel with the zero-padded transform (rsvd_align_best_fine)."""
+    _require_operands(cA, N_A, T, cB, N_B, H, Q, FP32)
     dev = cA.device
     best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
     arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
@@ -474,7 +543,10 @@ def align_best_fine(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: i
 def align_best_pairs(cA: torch.Tensor, N_A: int, T: int, cB: torch.Tensor, N_B: int, H: int, Q: int,
                      pairs: torch.Tensor, P: int = 1, inv_sigma2: float = 1.0, want_lse: bool = False, stream=None):
     """best / arg / lse for the (image, template) pairs int32 [K, 2]."""
+    _require_operands(cA, N_A, T, cB, N_B, H, Q, FP32)
     _require_cuda(pairs, torch.int32, "pairs")
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must be int32 [K, 2]")
     K = pairs.shape[0]
     dev = cA.device
     best = torch.empty((K,), dtype=torch.float32, device=dev)
@@ -512,6 +584,7 @@ def align_marching(coarse, fine, N_A: int, T: int, N_B: int, Q: int, keep: int, 
 
 def lse_rows(lse: torch.Tensor, stream=None) -> torch.Tensor:
     """L[n] = log sum_j exp(lse[n][j])."""
+    _require_cuda(lse, torch.float32, "lse")
     N_A, N_B = lse.shape
     L = torch.empty((N_A,), dtype=torch.float32, device=lse.device)
     check(lib().rsvd_lse_rows(_ptr(lse), N_A, N_B, _ptr(L), _stream(stream)), "rsvd_lse_rows")
@@ -520,6 +593,10 @@ def lse_rows(lse: torch.Tensor, stream=None) -> torch.Tensor:
 
 def lse_backward(cA, N_A, T, cB, N_B, H, Q, inv_sigma2, L, gL, precision: int = FP32, stream=None):
     """Gradients (gA, gB) of sum_n gL[n] L[n] with respect to the compressed rings."""
+    precision = _prec(precision)
+    _require_operands(cA, N_A, T, cB, N_B, H, Q, precision)
+    _require_out(L, (N_A,), torch.float32, "L")
+    _require_out(gL, (N_A,), torch.float32, "gL")
     gA = torch.empty_like(cA)
     gB = torch.empty_like(cB)
     need = int(lib().rsvd_lse_backward_workspace_bytes(N_A, T, N_B, H, Q))
@@ -534,6 +611,8 @@ def compress_backward(k, w, U: torch.Tensor, gC: torch.Tensor, N: int, R: int, Q
                       precision: int = FP32, stream=None) -> torch.Tensor:
     """Gradient with respect to the polar samples (complex64 [N, R, Q]) from the
     gradient with respect to the compressed rings (layout of compress)."""
+    precision = _prec(precision)
+    _require_U(U, R)
     H = U.shape[1]
     ka, kp = _host_f64(k)
     wa, wp = _host_f64(w)
@@ -542,6 +621,7 @@ def compress_backward(k, w, U: torch.Tensor, gC: torch.Tensor, N: int, R: int, Q
     else:
         da, dp = _host_f64(deltas)
         T = da.reshape(-1, 2).shape[0]
+    _require_dev_bytes(gC, compressed_bytes(N, T, H, Q, precision), "gC")
     out = torch.empty((N, R, Q), dtype=torch.complex64, device=gC.device)
     check(lib().rsvd_compress_backward(R, Q, kp, wp, _ptr(U), H, _ptr(gC), N, dp, T, precision, _ptr(out),
                                        _stream(stream)), "rsvd_compress_backward")

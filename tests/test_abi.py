@@ -131,3 +131,25 @@ def test_empty_inputs_are_argument_errors(lib):
     streams = (ctypes.c_void_p * 1)(None)
     assert fn("rsvd_align_grouped")(4, 16, kp, kp, one, one, 2, one, offs, 0, None, 1, one, 1, 0, one, one, one,
                                     1 << 20, streams, 1) == -1
+
+
+def test_binding_checks_buffers_before_calling(lib):
+    """The Python binding refuses host tensors, wrong shapes and dtypes before
+    any pointer reaches the library (these checks need no GPU)."""
+    import torch
+
+    import paper_2202_07235_gb300 as P
+
+    host = torch.zeros(1 << 16, dtype=torch.uint8)
+    with pytest.raises(TypeError):
+        P.align_best(host, 1, 1, host, 1, 8, 256)
+    with pytest.raises(TypeError):
+        P.align_scores(host, 1, 1, host, 1, 8, 256, precision="bf16")
+    with pytest.raises(TypeError):
+        P.lse_rows(torch.zeros((2, 3)))
+    with pytest.raises(TypeError):  # images must be in host memory for the host pipeline, U on the device
+        P.align_best_host([1.0], [1.0], torch.zeros((4, 2), dtype=torch.float64),
+                          torch.zeros((1, 4, 16), dtype=torch.complex64), torch.zeros((1, 4, 16), dtype=torch.complex64))
+    with pytest.raises(ValueError):  # templates with another ring count than the images
+        P.align_best_host([1.0], [1.0], torch.zeros((4, 2), dtype=torch.float64),
+                          torch.zeros((1, 4, 16), dtype=torch.complex64), torch.zeros((1, 5, 16), dtype=torch.complex64))

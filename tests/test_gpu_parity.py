@@ -218,3 +218,28 @@ def test_maximum_sizes_match_oracle():
     P.status()
     X, _, _ = oracle_scores(wl, A, B, U)
     check_best(X, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
+
+
+@pytest.mark.gpu
+def test_binding_rejects_short_buffers():
+    """Operand and output buffers smaller than the call's sizes are refused by
+    the binding (ValueError) before anything is launched."""
+    N_A, T, N_B, H, Q = 3, 2, 4, 8, 128
+    need_a = P.compressed_bytes(N_A, T, H, Q)
+    cA = torch.zeros(need_a // 4 - 1, dtype=torch.float32, device=DEV)
+    cB = torch.zeros(P.compressed_bytes(N_B, 1, H, Q) // 4, dtype=torch.float32, device=DEV)
+    with pytest.raises(ValueError):
+        P.align_best(cA, N_A, T, cB, N_B, H, Q)
+    cA = torch.zeros(need_a // 4, dtype=torch.float32, device=DEV)
+    with pytest.raises(ValueError):
+        P.align_scores(cA, N_A, T, cB, N_B + 1, H, Q)
+    best = torch.empty((N_A, N_B - 1), dtype=torch.float32, device=DEV)
+    arg = torch.empty((N_A, N_B), dtype=torch.int32, device=DEV)
+    with pytest.raises(ValueError):
+        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None))
+    with pytest.raises(ValueError):
+        P.pack(cA, N_A, T + 1, H, Q, "bf16")
+    P.status()
+    b, a, _ = P.align_best(cA, N_A, T, cB, N_B, H, Q)  # the exact sizes pass
+    P.status()
+    assert b.shape == (N_A, N_B) and a.shape == (N_A, N_B)

@@ -218,11 +218,16 @@ def test_single_pass_error_is_bounded(form, bound):
 
 
 def test_operand_forms_reject_unsupported_sizes():
-    x = torch.zeros(16, device=DEV)
+    def buf(H, Q, form):  # operand buffers large enough for the binding's size check
+        return torch.zeros(max(P.compressed_bytes(1, 1, H, Q, form), 64), dtype=torch.uint8, device=DEV)
+
+    x = buf(8, 512, "bf16")
     with pytest.raises(P.RSVDError):
         P.align_best(x, 1, 1, x, 1, 8, 512, precision="bf16")
+    x = buf(33, 256, "bf16x3")
     with pytest.raises(P.RSVDError):
         P.align_best(x, 1, 1, x, 1, 33, 256, precision="bf16x3")
+    x = buf(20, 256, "bf16x3")
     with pytest.raises(P.RSVDError):  # split operands at Q = 256: shared memory holds H <= 18
         P.align_best(x, 1, 1, x, 1, 20, 256, precision="bf16x3")
     assert P.compressed_bytes(4, 1, 8, 64, "bf16") == 0
