@@ -429,7 +429,8 @@ def run_ours(args):
     achieved = flops / (align_avg_ms / 1e3) / 1e12
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
-    kname = f"ws_align_kernel<{Q // 2},{12 if H <= 12 else 16}>" if (Q == 256 and H <= 16) else "fused_align_kernel"
+    hp = 8 if H <= 8 else 12 if H <= 12 else 16
+    kname = f"ws_align_kernel<{Q // 2},{hp}>" if (Q in (256, 512) and H <= 16) else "fused_align_kernel"
     if prec == "fp32":
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
                     "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),

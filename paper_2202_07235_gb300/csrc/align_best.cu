@@ -57,6 +57,7 @@ extern "C" int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, i
   rc = RSVD_EUNSUPPORTED;
   if (HP > 0) {
     if (Q == 256 && !classic) rc = launch_ws_s128(HP, p, st);
+    if (Q == 512 && !classic) rc = launch_ws_s256(HP, p, st);
     if (rc == RSVD_EUNSUPPORTED) {
       if (Q == 128) rc = launch_fused_s64(HP, p, st);
       else if (Q == 256) rc = launch_fused_s128(HP, p, st);

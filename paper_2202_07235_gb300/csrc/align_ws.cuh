@@ -1,4 +1,4 @@
-// Warp-specialised fused scoring kernel (rsvd_align_best, FP32, Q/2 <= 128).
+// Warp-specialised fused scoring kernel (rsvd_align_best, FP32, Q = 256 and 512).
 //
 // Same arithmetic as fused_align_kernel (eq. image_innerproduct_pm Steps 1-2,
 // section 2.7 argmax, section 2.6 log-sum-exp), with the two phases running
@@ -7,7 +7,7 @@
 // * contraction warps (CT threads = GC row groups x S angular slots) hold RT
 //   image rows per slot in registers and write the half spectra of RP x TB
 //   (row, template) pairs into one of two spectrum buffers;
-// * FFT warps (256 threads, P2 lanes per pair) take a full buffer, run the C2R
+// * FFT warps (FT threads, P2 lanes per pair) take a full buffer, run the C2R
 //   FFT and the max/argmax/log-sum-exp of each pair, release the buffer, and
 //   merge the rows of each image into the outputs.
 // Hand-offs use named barriers (FULL[i]: contraction -> FFT, FREE[i]: FFT ->
@@ -22,13 +22,18 @@
 
 namespace rsvd {
 
+// S = 128: 256 contraction + 256 FFT threads, 3 image rows per thread (H <= 12).
+// S = 256: one template (H <= 16) takes 32 KB of shared memory, so a batch holds
+// two; 4 image rows per contraction thread (the 384-thread block leaves 168
+// registers per thread) make 8 pairs per batch, the work of 128 FFT threads.
 template <int S, int HP>
 struct WsCfg {
   static constexpr int P1 = FftSplit<S>::P1, P2 = FftSplit<S>::P2, F = P2, RR = P1 / P2;
-  static constexpr int RT = cmax(1, cmin(4, 36 / HP));  // image rows per contraction thread
+  static constexpr bool kWide = S >= 256;
+  static constexpr int RT = kWide ? cmax(1, cmin(4, 64 / HP)) : cmax(1, cmin(4, 36 / HP));  // rows per thread
   static constexpr int GC = cmax(1, 256 / S);            // contraction row groups
   static constexpr int CT = GC * S;                      // contraction threads
-  static constexpr int FT = 256;                         // FFT threads
+  static constexpr int FT = kWide ? 128 : 256;           // FFT threads
   static constexpr int NT = CT + FT;
   static constexpr int RP = GC * RT;                     // rows per pass
   static constexpr int PGF = FT / F;                     // pairs per FFT round
@@ -41,7 +46,7 @@ struct WsCfg {
   static constexpr int SPB = PAIRS + (PGF - PAIRS % PGF) % PGF;  // pair regions per buffer (incl. dummies)
   static constexpr size_t SMEM = (size_t)2 * TB * HP * S * 8 + (size_t)2 * SPB * SP * 8 + (size_t)2 * S * 8 +
                                  (size_t)2 * 3 * PAIRS * 4 + 64;
-  static constexpr bool kFits = SMEM <= 227 * 1024 && S <= 128 && TB_SMEM >= 1;
+  static constexpr bool kFits = SMEM <= 227 * 1024 && S <= 256 && TB_SMEM >= 1;
 };
 
 // clock budget of one bounded wait (about half a second at 2 GHz)
@@ -391,5 +396,6 @@ int launch_ws_cfg(const FusedParams& p0, cudaStream_t stream) {
 }
 
 RSVD_HIDDEN int launch_ws_s128(int HP, const FusedParams& p, cudaStream_t stream);
+RSVD_HIDDEN int launch_ws_s256(int HP, const FusedParams& p, cudaStream_t stream);
 
 }  // namespace rsvd
