@@ -153,3 +153,24 @@ def test_binding_checks_buffers_before_calling(lib):
     with pytest.raises(ValueError):  # templates with another ring count than the images
         P.align_best_host([1.0], [1.0], torch.zeros((4, 2), dtype=torch.float64),
                           torch.zeros((1, 4, 16), dtype=torch.complex64), torch.zeros((1, 5, 16), dtype=torch.complex64))
+
+
+def test_plain_c_client_compiles_links_and_runs(lib, tmp_path):
+    """tests/c_abi_check.c, a C99 program using only include/rsvd.h, builds
+    against librsvd.so with gcc and its no-GPU checks pass."""
+    import shutil
+    import subprocess
+
+    from paper_2202_07235_gb300 import build as B
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(B.LIB)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I" + os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_abi_check.c"), "-o", exe, "-L" + libdir, "-lrsvd",
+                    "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert "c abi ok" in r.stdout
