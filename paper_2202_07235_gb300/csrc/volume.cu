@@ -19,6 +19,8 @@
 //   running max / argmax over (beta, alpha, gamma).
 #include <math.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "align_common.cuh"
@@ -206,7 +208,18 @@ struct VolAlignParams {
   int32_t* arg;
   const double* V;   // dev [L+1][HD]
   int N_A, N_B, HC, L, HD, n_beta;
+  // chunk[w * kVolMaxEPT + q]: the 32-entry chunk of the (m1, m2) half grid that
+  // warp w holds in slot q (see vol_chunk_plan)
+  uint8_t chunk[16 * 4];
 };
+
+constexpr int kVolMaxEPT = 4;
+
+// Entry of the (m1, m2) half grid (e = (m1 + L) M + m2 + L < (M^2 + 1) / 2) that
+// thread tid holds in slot q; entries past the half grid are unused slots.
+__device__ __forceinline__ int vol_entry(const VolAlignParams& p, int tid, int q) {
+  return (int)p.chunk[(tid >> 5) * kVolMaxEPT + q] * 32 + (tid & 31);
+}
 
 
 // Forward 8-point DFT (kernel e^{-2 pi i n k / 8}) in place, natural order in
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_c
   for (int q = 0; q < EPT; ++q) {
 #pragma unroll
     for (int d = 0; d < kVolMaxHD; ++d) Y[q][d] = make_float2(0.f, 0.f);
-    const int e = tid + q * kAlignThreads;
+    const int e = vol_entry(p, tid, q);
     const bool on = e < Mh;
     const int i1 = on ? e / M : 0, i2 = on ? e % M : 0;
     const int l0 = on ? max(abs(i1 - L), abs(i2 - L)) : L + 1;
@@ -398,7 +411,7 @@ __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_c
     int off[EPT], offm[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
-      const int e = min(tid + q * kAlignThreads, Mh - 1);
+      const int e = min(vol_entry(p, tid, q), Mh - 1);
       const int m1 = e / M - L, m2 = e % M - L;
       off[q] = ((m1 + 64) & 63) * kS + ((m2 + 64) & 63);
       offm[q] = ((64 - m1) & 63) * kS + ((64 - m2) & 63);
@@ -408,7 +421,7 @@ __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_c
       const float* T2 = b + 1 < p.n_beta ? T1 + (size_t)MM * kVolMaxHD : T1;
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * kAlignThreads;
+        const int e = vol_entry(p, tid, q);
         if (e < Mh) {
           float* dst = Ts + ((q * 2) * kAlignThreads + tid) * kVolMaxHD;
           cp_async16(dst, T1 + (size_t)e * kVolMaxHD);
@@ -428,7 +441,7 @@ __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_c
       // Step 2 at m and -m
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * kAlignThreads;
+        const int e = vol_entry(p, tid, q);
         if (e < Mh) {
           const float* t = Ts + ((q * 2) * kAlignThreads + tid) * kVolMaxHD;
           const float4 a0 = *reinterpret_cast<const float4*>(t), a1 = *reinterpret_cast<const float4*>(t + 4);
@@ -516,7 +529,7 @@ __global__ void __launch_bounds__(kAlignThreads) vol_align_kernel(const __grid_c
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * kAlignThreads;
+        const int e = vol_entry(p, tid, q);
         if (e < Mh) {
           float2 h1 = make_float2(0.f, 0.f), h2 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -699,6 +712,35 @@ extern "C" int rsvd_compress_volume(int R, int L, const double* w, const double*
 
 namespace rsvd {
 namespace {
+
+// Step 1 of a (m1, m2) entry loops over l = max(|m1|, |m2|) .. L, and a warp runs
+// as many iterations as its entry with the smallest l; the first half grid is
+// cut into 32-entry chunks (one per warp and slot) and the chunks are dealt to
+// the 16 warps, heaviest first, each to the warp with the least work so far
+// that still has a free slot, so that no warp carries much more Step-1 work
+// than the mean (at L = 24: 33 iterations for the busiest warp instead of 44).
+void vol_chunk_plan(int L, int ept, uint8_t* chunk) {
+  const int M = 2 * L + 1, Mh = (M * M + 1) / 2, warps = kAlignThreads / 32, n = warps * ept;
+  int work[16 * kVolMaxEPT], order[16 * kVolMaxEPT], load[16] = {0}, used[16] = {0};
+  for (int c = 0; c < n; ++c) {
+    int lmin = L + 1;
+    for (int e = 32 * c; e < 32 * c + 32 && e < Mh; ++e) {
+      const int a = abs(e / M - L), b = abs(e % M - L);
+      lmin = std::min(lmin, std::max(a, b));
+    }
+    work[c] = L + 1 - lmin;
+    order[c] = c;
+  }
+  std::stable_sort(order, order + n, [&](int x, int y) { return work[x] > work[y]; });
+  for (int i = 0; i < n; ++i) {
+    int w = -1;
+    for (int k = 0; k < warps; ++k)
+      if (used[k] < ept && (w < 0 || load[k] < load[w])) w = k;
+    chunk[w * kVolMaxEPT + used[w]++] = (uint8_t)order[i];
+    load[w] += work[order[i]];
+  }
+}
+
 int align_volumes_impl(bool real, const void* cA, int N_A, const void* cB, int N_B, int HC, int L, const double* V,
                        int HD, const float* tables, int n_beta, int Mp, float* best, int32_t* arg, void* stream) {
   if (!cA || !cB || !V || !tables || !best || !arg || N_A <= 0 || N_B <= 0 || HC <= 0 || L < 1 || HD <= 0 ||
@@ -723,6 +765,8 @@ int align_volumes_impl(bool real, const void* cA, int N_A, const void* cB, int N
   ap.n_beta = n_beta;
   const int M = 2 * L + 1;
   const int ept = ((M * M + 1) / 2 + kAlignThreads - 1) / kAlignThreads;
+  if (ept > kVolMaxEPT) return RSVD_EUNSUPPORTED;
+  vol_chunk_plan(L, Mp == 64 ? ept : 1, ap.chunk);
   const size_t smem = vol_align_layout(HC, L, Mp).total;
   if (smem > 227 * 1024) return RSVD_EUNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
