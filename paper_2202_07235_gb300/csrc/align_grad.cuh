@@ -49,7 +49,7 @@ struct GradCfg {
   static constexpr int RP = G * RT;
   static constexpr int XP = P2 + 1;
   static constexpr int SP = pair_stride(S, P1, P2);
-  static constexpr int kBudget = 200 * 1024;
+  static constexpr int kBudget = 216 * 1024;
   static constexpr int FIXED = 2 * S * 8 + 8 * RP + 256;
   static constexpr int PER_TB = 2 * HP * S * 8 + RP * SP * 8 + 8;
   static constexpr int TB = cmax(1, cmin(16, (kBudget - FIXED) / PER_TB));
