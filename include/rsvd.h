@@ -81,6 +81,17 @@ const char* rsvd_strerror(int code);
  * synchronisation itself failed. */
 int rsvd_status(void* stream);
 
+/* Self-test of the device-side failure path that every bounded wait of the
+ * library takes: enqueues one tiny kernel whose thread waits on an mbarrier
+ * that nothing arrives on, with the same clock-bounded wait the scoring
+ * kernels use; after `budget_cycles` SM clock cycles (1 .. 2^31, about a
+ * second at most) the wait gives up and records RSVD_ETIMEOUT in the status
+ * word, and the kernel returns. A following rsvd_status(stream) then reports
+ * RSVD_ETIMEOUT and clears it; the CUDA context stays usable. Returns
+ * RSVD_EINVAL for a budget outside that range, else RSVD_OK / RSVD_ECUDA
+ * for the launch. */
+int rsvd_selftest_wait_timeout(long long budget_cycles, void* stream);
+
 /* ------------------------------------------------------------------------
  * Precompute: ring-ring kernel C and its principal vectors.
  * Paper section 3.3, eq. (Image_simple_kern): C_{rr'} is proportional to

@@ -36,6 +36,7 @@ from .api import (  # noqa: F401
     lse_rows,
     pack,
     select_pairs,
+    selftest_wait_timeout,
     status,
     volume_tables,
 )

@@ -26,6 +26,7 @@ SIGNATURES = {
     "rsvd_abi_version": (c_int, []),
     "rsvd_strerror": (ctypes.c_char_p, [c_int]),
     "rsvd_status": (c_int, [c_void_p]),
+    "rsvd_selftest_wait_timeout": (c_int, [ctypes.c_longlong, c_void_p]),
     "rsvd_build_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
     "rsvd_build_radial_svd": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                       c_size_t, c_void_p]),

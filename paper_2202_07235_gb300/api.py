@@ -665,6 +665,15 @@ def lse_align(images, templates, U, k, w, deltas=None, inv_sigma2: float = 1.0) 
     return LSEAlign.apply(images, templates, U, k, w, deltas, inv_sigma2)
 
 
+def selftest_wait_timeout(budget_cycles: int = 1 << 21, stream=None) -> int:
+    """Runs the bounded-wait self-test (rsvd_selftest_wait_timeout: a device
+    wait on a barrier that nothing completes) and returns the status code it
+    leaves, read and cleared by rsvd_status: RSVD_ETIMEOUT (-5) when the
+    failure path works."""
+    check(lib().rsvd_selftest_wait_timeout(int(budget_cycles), _stream(stream)), "rsvd_selftest_wait_timeout")
+    return int(lib().rsvd_status(_stream(stream)))
+
+
 def status(stream=None) -> None:
     """Synchronises the stream and raises if a kernel recorded a device-side failure."""
     check(lib().rsvd_status(_stream(stream)), "rsvd_status")

@@ -3,6 +3,7 @@
 #include <mutex>
 
 #include "operand.cuh"
+#include "ptx_sync.cuh"
 
 namespace rsvd {
 
@@ -24,9 +25,32 @@ RSVD_HIDDEN int* status_word() {
   return ptrs[dev];
 }
 
+namespace {
+
+// One thread waits on an mbarrier whose phase never completes (nothing
+// arrives), with the bounded wait of the scoring kernels.
+__global__ void wait_selftest_kernel(int* status, long long budget) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, budget)) record(status, kDevTimeout);
+}
+
+}  // namespace
 }  // namespace rsvd
 
 extern "C" {
+
+int rsvd_selftest_wait_timeout(long long budget_cycles, void* stream) {
+  if (budget_cycles < 1 || budget_cycles > (1LL << 31)) return RSVD_EINVAL;
+  int* status = rsvd::status_word();
+  if (!status) return RSVD_ECUDA;
+  rsvd::wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(status, budget_cycles);
+  return rsvd::launch_status();
+}
 
 int rsvd_abi_version(void) { return RSVD_ABI_VERSION; }
 

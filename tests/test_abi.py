@@ -174,3 +174,13 @@ def test_plain_c_client_compiles_links_and_runs(lib, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     assert "c abi ok" in r.stdout
+
+
+def test_wait_selftest_rejects_a_bad_budget(lib):
+    """The bounded-wait self-test checks its budget before any CUDA call."""
+    from paper_2202_07235_gb300._native import SIGNATURES
+
+    f = lib.rsvd_selftest_wait_timeout
+    f.restype, f.argtypes = SIGNATURES["rsvd_selftest_wait_timeout"]
+    assert f(0, None) == -1
+    assert f((1 << 31) + 1, None) == -1
