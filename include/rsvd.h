@@ -396,6 +396,7 @@ int rsvd_align_volumes_real(const void* cA, int N_A, const void* cB, int N_B, in
  *              ring is copied, the samples the compression reads);
  *   best, arg  host [N_A][N_B] (lse host [N_A][N_B] or NULL): as rsvd_align_best;
  *   chunk      images per pipeline stage (e.g. a multiple of 2 x the SM count);
+ *              the first stage takes chunk / 4 (chunk >= 8) to shorten the fill;
  *   workspace  device, >= rsvd_align_host_workspace_bytes(R, Q, H, T, N_B,
  *              chunk, precision, lse != NULL), 256-byte aligned, caller-owned;
  *   stream     runs the kernels; copy_stream (a different stream) runs the

@@ -102,7 +102,13 @@ extern "C" int rsvd_align_best_host(int R, int Q, const double* k, const double*
   auto h2d = [&](void* dst, const void* src, size_t rings) {  // psi < pi of each ring
     return cudaMemcpy2DAsync(dst, pitch, src, pitch, half, rings, cudaMemcpyHostToDevice, cp) == cudaSuccess;
   };
-  const int nchunk = (N_A + chunk - 1) / chunk;
+  // The first chunk is a quarter of the others: the first alignment waits for
+  // the templates and the whole first chunk to arrive, and a smaller first
+  // chunk shortens that fill; the later copies hide behind the kernels.
+  const int first = chunk >= 8 ? chunk / 4 : chunk;
+  const int nchunk = 1 + (N_A - first + chunk - 1) / chunk;
+  auto start = [&](int c) { return c == 0 ? 0 : first + (c - 1) * chunk; };
+  auto count = [&](int c) { return c == 0 ? min(first, N_A) : min(chunk, N_A - start(c)); };
   // templates: copy (copy stream), compress (compute stream)
   if (!h2d(tpolar, templates, (size_t)N_B * R)) return RSVD_ECUDA;
   if (cudaEventRecord(ev_back[1], cp) != cudaSuccess || cudaStreamWaitEvent(st, ev_back[1], 0) != cudaSuccess)
@@ -110,14 +116,14 @@ extern "C" int rsvd_align_best_host(int R, int Q, const double* k, const double*
   int rc = rsvd_compress(R, Q, k, w, U, H, tpolar, N_B, nullptr, 1, precision, cB, stream);
   if (rc != RSVD_OK) return rc;
   auto copy_in = [&](int c) -> int {
-    const int b = c & 1, n0 = c * chunk, n = min(chunk, N_A - n0);
+    const int b = c & 1, n0 = start(c), n = count(c);
     if (c >= 2 && cudaStreamWaitEvent(cp, ev_used[b], 0) != cudaSuccess) return RSVD_ECUDA;
     if (!h2d(polar[b], static_cast<const char*>(images) + (size_t)n0 * R * pitch, (size_t)n * R)) return RSVD_ECUDA;
     return cudaEventRecord(ev_in[b], cp) == cudaSuccess ? RSVD_OK : RSVD_ECUDA;
   };
   if ((rc = copy_in(0)) != RSVD_OK) return rc;
   for (int c = 0; c < nchunk; ++c) {
-    const int b = c & 1, n0 = c * chunk, n = min(chunk, N_A - n0);
+    const int b = c & 1, n0 = start(c), n = count(c);
     if (c + 1 < nchunk && (rc = copy_in(c + 1)) != RSVD_OK) return rc;  // overlaps chunk c's work
     if (cudaStreamWaitEvent(st, ev_in[b], 0) != cudaSuccess) return RSVD_ECUDA;
     rc = rsvd_compress(R, Q, k, w, U, H, polar[b], n, deltas, T, precision, cA, stream);
