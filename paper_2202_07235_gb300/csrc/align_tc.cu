@@ -117,6 +117,37 @@ __device__ __forceinline__ void issue_group(uint32_t leader, uint32_t d, uint64_
   }
 }
 
+// Single-pass chains of two groups with their K-steps interleaved (each chain
+// accumulates into its own TMEM columns, so consecutive MMAs never wait on one
+// another's accumulator).
+template <int KS>
+__device__ __forceinline__ void issue_two_groups(uint32_t leader, uint32_t d0, uint32_t d1, uint64_t ad0, uint64_t bd0,
+                                                 uint64_t ad1, uint64_t bd1, uint64_t a_step, uint64_t b_step,
+                                                 uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    tc_mma_f16_by(leader, d0, ad0 + ks * a_step, bd0 + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+    tc_mma_f16_by(leader, d1, ad1 + ks * a_step, bd1 + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+  }
+}
+
+__device__ __forceinline__ void issue_two_groups_rt(int KS, uint32_t leader, uint32_t d0, uint32_t d1, uint64_t ad0,
+                                                    uint64_t bd0, uint64_t ad1, uint64_t bd1, uint64_t a_step,
+                                                    uint64_t b_step, uint32_t idesc) {
+  switch (KS) {
+    case 2: issue_two_groups<2>(leader, d0, d1, ad0, bd0, ad1, bd1, a_step, b_step, idesc); return;
+    case 3: issue_two_groups<3>(leader, d0, d1, ad0, bd0, ad1, bd1, a_step, b_step, idesc); return;
+    case 4: issue_two_groups<4>(leader, d0, d1, ad0, bd0, ad1, bd1, a_step, b_step, idesc); return;
+    case 6: issue_two_groups<6>(leader, d0, d1, ad0, bd0, ad1, bd1, a_step, b_step, idesc); return;
+    case 8: issue_two_groups<8>(leader, d0, d1, ad0, bd0, ad1, bd1, a_step, b_step, idesc); return;
+    default:
+      for (int ks = 0; ks < KS; ++ks) {
+        tc_mma_f16_by(leader, d0, ad0 + ks * a_step, bd0 + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+        tc_mma_f16_by(leader, d1, ad1 + ks * a_step, bd1 + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+      }
+  }
+}
+
 template <bool kSplit>
 __device__ __forceinline__ void issue_group_rt(int KS, uint32_t leader, uint32_t d, uint64_t ad, uint64_t bd,
                                                uint64_t ad_lo, uint64_t bd_lo, uint64_t a_step, uint64_t b_step,
@@ -259,7 +290,10 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
   return make_float4(best, __int_as_float(bm), lm, ls);
 }
 
-template <int Q, bool kWriteX>
+// kPair: single-pass forms with resident template blocks (the producers only
+// issue copies) take two groups from two consecutive stages per MMA step, their
+// chains interleaved; the other plans keep one group per step.
+template <int Q, bool kWriteX, bool kPair>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_constant__ TcParams p) {
   using C = TcCfg<Q>;
   constexpr int g = C::g, NT = C::NT, TPT = C::TPT;
@@ -488,7 +522,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
             break;
           }
           tc_fence_after();
-          for (int grp = 0; grp < kOpGroups; ++grp) {
+          for (int grp = 0; kPair && grp < kOpGroups; grp += 2) {
+            const int s0 = ms;
+            const uint32_t ph0 = mphase;
+            const int s1 = (ms + 1 == p.stages) ? 0 : ms + 1;
+            const uint32_t ph1 = (ms + 1 == p.stages) ? (mphase ^ 1u) : mphase;
+            if (!__all_sync(0xffffffffu, tc_wait(&full[s0], ph0, abort_flag, p.status)) ||
+                !__all_sync(0xffffffffu, tc_wait(&full[s1], ph1, abort_flag, p.status))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t a_step = (2u * a_lbo) >> 4, b_step = (2u * b_lbo) >> 4;
+            const uint64_t ad0 = smem_desc_kmajor(smem_addr(tc_smem + (size_t)s0 * p.stage_bytes), a_lbo, kSbo);
+            const uint64_t ad1 = smem_desc_kmajor(smem_addr(tc_smem + (size_t)s1 * p.stage_bytes), a_lbo, kSbo);
+            const uint64_t bd0 = smem_desc_kmajor(smem_addr(tc_smem + p.bres_off + (size_t)grp * p.b_bytes), b_lbo, kSbo);
+            const uint64_t bd1 =
+                smem_desc_kmajor(smem_addr(tc_smem + p.bres_off + (size_t)(grp + 1) * p.b_bytes), b_lbo, kSbo);
+            issue_two_groups_rt(p.KS, mma_leader, tmem_base + (uint32_t)(grp * 16), tmem_base + (uint32_t)(grp * 16 + 16),
+                                ad0, bd0, ad1, bd1, a_step, b_step, p.idesc);
+            tc_commit_by(mma_leader, &empty[s0]);
+            tc_commit_by(mma_leader, &empty[s1]);
+            __syncwarp();
+            it += 2;
+            ms = (s1 + 1 == p.stages) ? 0 : s1 + 1;
+            mphase = (s1 + 1 == p.stages) ? (ph1 ^ 1u) : ph1;
+          }
+          for (int grp = 0; !kPair && grp < kOpGroups; ++grp) {
             const int s = ms;
             if (!__all_sync(0xffffffffu, tc_wait(&full[s], mphase, abort_flag, p.status))) {
               ok = false;
@@ -679,7 +739,9 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   p.nUnits = (int)units;
   const int grid = (int)(units < sms ? units : sms);
 
-  auto kern = write_x ? tc_align_kernel<Q, true> : tc_align_kernel<Q, false>;
+  const bool pair = p.bres && !p.split;
+  auto kern = write_x ? (pair ? tc_align_kernel<Q, true, true> : tc_align_kernel<Q, true, false>)
+                      : (pair ? tc_align_kernel<Q, false, true> : tc_align_kernel<Q, false, false>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return RSVD_ECUDA;
   kern<<<grid, kTcThreads, smem, stream>>>(p);
