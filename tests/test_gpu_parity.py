@@ -99,6 +99,8 @@ CASES = [
     (256, 64, 64, 2, 3, 5),      # H = 64 (widest register block), 4 translations
     (256, 40, 20, 1, 9, 11),     # H padded to 24
     (512, 48, 16, 2, 5, 4),      # Q = 512
+    (512, 40, 12, 3, 9, 5),      # Q = 512, H = 12: two passes per image group, three template batches
+    (512, 32, 7, 1, 13, 3),      # Q = 512, H padded to 8, ragged pass
     (128, 24, 1, 1, 3, 3),       # H = 1
     (16, 6, 3, 1, 4, 3),         # Q = 16 (generic per-pair path)
     (1024, 20, 5, 1, 2, 3),      # Q = 1024 (generic per-pair path)
