@@ -250,6 +250,10 @@ int rsvd_align_scores(const void* cA, int N_A, int T, const void* cB, int N_B, i
  *   lse[n][j]  = log sum_{t, m} exp(inv_sigma2 * X[n][t][j][m])   (if lse != NULL)
  *
  *   best dev float [N_A][N_B], arg dev int32 [N_A][N_B], lse dev float [N_A][N_B] or NULL
+ *
+ * FP32 at Q = 256 and 512 (H <= 16) runs the warp-specialised kernel; with
+ * the environment variable RSVD_ALIGN_KERNEL=fused it runs the single-role
+ * fused kernel instead (same results, for cross-checks and measurements).
  * ------------------------------------------------------------------------ */
 int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
                     int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
