@@ -253,7 +253,8 @@ int rsvd_align_scores(const void* cA, int N_A, int T, const void* cB, int N_B, i
  *
  * FP32 at Q = 256 and 512 (H <= 16) runs the warp-specialised kernel; with
  * the environment variable RSVD_ALIGN_KERNEL=fused it runs the single-role
- * fused kernel instead (same results, for cross-checks and measurements).
+ * fused kernel instead (the same values up to rounding; for cross-checks and
+ * measurements).
  * ------------------------------------------------------------------------ */
 int rsvd_align_best(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
                     int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
