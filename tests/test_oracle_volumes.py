@@ -131,3 +131,20 @@ def test_real_volumes_mirror_product():
     m = np.arange(-L, L + 1)
     s = (-1.0) ** (m[:, None] - m[None, :])
     assert np.allclose(s * np.conj(x[..., ::-1, ::-1]), x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+def test_volume_align_best_takes_the_first_maximum():
+    """max / argmax over (beta, alpha, gamma) by loops; equal maxima go to the
+    smallest flat index b Mp^2 + a Mp + c."""
+    rng = np.random.default_rng(9)
+    X = rng.integers(0, 4, size=(2, 3, 2, 3, 3)).astype(np.float64)  # many exact ties
+    best, arg = V.volume_align_best(X)
+    for n in range(2):
+        for j in range(3):
+            bv, bi = -np.inf, -1
+            for b in range(2):
+                for a in range(3):
+                    for c in range(3):
+                        if X[n, j, b, a, c] > bv:
+                            bv, bi = X[n, j, b, a, c], b * 9 + a * 3 + c
+            assert best[n, j] == bv and arg[n, j] == bi
