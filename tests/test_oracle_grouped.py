@@ -33,3 +33,19 @@ def test_noiseless_grouped_alignment_recovers_template_and_pose():
     T = wl.deltas.shape[0]
     assert np.array_equal(np.argmax(best, axis=1), wl.truth_j)
     assert np.array_equal(arg[np.arange(12), wl.truth_j], wl.truth_t * 64 + wl.truth_m)
+
+
+def test_group_vectors_are_the_principal_vectors_of_the_corrected_kernel():
+    """U_g diagonalises diag(ctf_g) C diag(ctf_g) (C the kernel of the uncorrected
+    templates) with its eigenvalues in decreasing order: the eigenvalues equal a
+    textbook symmetric eigen-solve of that matrix."""
+    wl = make_grouped_workload(N=32, R=16, Q=32, N_B=6, N_A=3, G=3, snr=None, seed=4)
+    C = O.radial_kernel(wl.templates, wl.grid.w)
+    H = 5
+    U, lam = O.grouped_principal_vectors(wl.templates, wl.grid.w, wl.ctf, H)
+    for g in range(3):
+        Kg = np.outer(wl.ctf[g], wl.ctf[g]) * C
+        ev = np.sort(np.linalg.eigvalsh(Kg))[::-1]
+        assert np.allclose(lam[g], ev, rtol=0, atol=1e-12 * ev[0])
+        D = U[g].T @ Kg @ U[g]
+        assert np.allclose(D, np.diag(ev[:H]), rtol=0, atol=1e-11 * ev[0])
