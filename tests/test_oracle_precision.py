@@ -110,3 +110,23 @@ def test_form_errors_follow_the_rounding_bounds():
         Xhat = sum(2 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(A), B) for A, B in kept)
         e = np.linalg.norm(np.fft.fft(Xhat, axis=-1).real - X) / nrm
         assert e > 10 * err["bf16x3"], drop
+
+
+def test_every_operand_is_a_value_of_its_format():
+    """The tensor cores take bf16 (or fp16) values only: every operand of the
+    single-pass forms, and the hi and lo parts of the split form, is unchanged by
+    rounding to that format (checked against torch's conversion)."""
+    rng = np.random.default_rng(11)
+    a = (rng.standard_normal((2, 1, 3, 16)) + 1j * rng.standard_normal((2, 1, 3, 16))) * 3.7
+    b = (rng.standard_normal((2, 3, 16)) + 1j * rng.standard_normal((2, 3, 16))) * 0.01
+
+    def representable(z, dtype):
+        for part in (z.real, z.imag):
+            t = torch.from_numpy(np.ascontiguousarray(part)).to(torch.float32)
+            if not np.array_equal(t.to(dtype).to(torch.float64).numpy(), part):
+                return False
+        return True
+
+    for form, dtype in (("bf16", torch.bfloat16), ("fp16", torch.float16), ("bf16x3", torch.bfloat16)):
+        for A, B in O.operand_terms(a, b, form):
+            assert representable(A, dtype) and representable(B, dtype), form
