@@ -184,3 +184,28 @@ def test_wait_selftest_rejects_a_bad_budget(lib):
     f.restype, f.argtypes = SIGNATURES["rsvd_selftest_wait_timeout"]
     assert f(0, None) == -1
     assert f((1 << 31) + 1, None) == -1
+
+
+def test_binding_rejects_host_tensors_everywhere(lib):
+    """Every device-side argument of the binding must be a CUDA tensor; a host
+    tensor is refused before any pointer reaches the library."""
+    import torch
+
+    import paper_2202_07235_gb300 as P
+
+    w = [1.0] * 4
+    polar = torch.zeros((2, 4, 16), dtype=torch.complex64)
+    U = torch.zeros((4, 2), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        P.build_radial_svd(w, polar, 2)
+    with pytest.raises(TypeError):
+        P.compress(w, w, U, polar)
+    with pytest.raises(TypeError):
+        P.pack(torch.zeros(64), 1, 1, 2, 16, "bf16")
+    vols = torch.zeros((1, 4, 3, 5), dtype=torch.complex64)
+    with pytest.raises(TypeError):
+        P.compress_volume(w, U, vols)
+    with pytest.raises(TypeError):
+        P.align_volumes(vols, vols, torch.zeros((3, 2), dtype=torch.float64), torch.zeros((2, 5, 5, 8)), 16)
+    with pytest.raises(TypeError):
+        P.select_pairs(torch.zeros((2, 3)), 1)
