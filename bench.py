@@ -54,10 +54,20 @@ def _oracle_images(images):
     two-step score against all templates, max/argmax. Returns (best, arg)."""
     import oracle as O
 
+    import numpy as np
+
     A_t = O.translate(images, _W["k"], _W["deltas"])
     a_c = O.compress(A_t, _W["U"], _W["w"])
-    X = O.scores_compressed(a_c, _W["b_c"]).real
-    return O.align_best(X)
+    # templates in blocks of 512 (bounded memory: X of one block is
+    # images x T x 512 x Q complex); pairs are independent
+    b_c = _W["b_c"]
+    bests, args = [], []
+    for j0 in range(0, b_c.shape[0], 512):
+        X = O.scores_compressed(a_c, b_c[j0:j0 + 512]).real
+        b, a = O.align_best(X)
+        bests.append(b)
+        args.append(a)
+    return np.concatenate(bests, axis=1), np.concatenate(args, axis=1)
 
 
 def _cores():
@@ -150,12 +160,14 @@ def _workload_desc(cfg):
             f"({cfg['T_side']}x{cfg['T_side']}, 1 px), H={cfg['H']}, SNR {cfg['snr']}")
 
 
-def _alg_flops_per_pair(H, Q):
+def _alg_flops_per_pair(H, Q, real_fft=False):
     """Algorithmic FP32 work per (image, translation, template) pair: the
     half-spectrum contraction (8 flops per complex multiply-add, Q/2+1
-    frequencies), a C2R FFT of length Q (2.5 Q log2 Q) and the reduction
-    (2 ops per score)."""
-    return 8 * H * (Q // 2 + 1) + 2.5 * Q * math.log2(Q) + 2 * Q
+    frequencies), a C2R FFT of length Q (2.5 Q log2 Q, the complex-FFT count;
+    1.25 Q log2 Q with real_fft, the count of a real-output transform) and the
+    reduction (2 ops per score)."""
+    fft = (1.25 if real_fft else 2.5) * Q * math.log2(Q)
+    return 8 * H * (Q // 2 + 1) + fft + 2 * Q
 
 
 def _load_traffic(kernel_key):
@@ -199,7 +211,8 @@ def _form_roofline(P, fp, N_A, N_B, T, H, Q, align_ms, sm_count):
     nbytes = P.compressed_bytes(N_A, T, H, Q, fp) + P.compressed_bytes(N_B, 1, H, Q, fp) + N_A * N_B * 8
     pk = _peaks()
     peak_t = pk.get("bf16_tflops_sustained") or 1700.0
-    peak_a = sm_count * 128 * 2 * 2.07e9 / 1e12
+    rates = next(iter(_RATES.values()), None)
+    peak_a = rates["fp32_tflops"] if rates else sm_count * 128 * 2 * 2.07e9 / 1e12
     peak_h = pk.get("hbm_gbs") or 6800.0
     floors = {"tensor": gemm / (peak_t * 1e12) * 1e3, "alu": fft / (peak_a * 1e12) * 1e3,
               "hbm": nbytes / (peak_h * 1e9) * 1e3}
@@ -219,7 +232,8 @@ def _form_roofline(P, fp, N_A, N_B, T, H, Q, align_ms, sm_count):
     return {"bound": bound, "kernel": f"tc_align_kernel<{Q},false>", "achieved": round(work / sec, 2),
             "peak": round(peak, 2), "unit": unit, "frac": round(floors[bound] / align_ms, 4),
             "floors_ms": {k: round(v, 3) for k, v in floors.items()},
-            "peak_basis": (f"transform + reduction flops; {sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
+            "peak_basis": (("transform + reduction flops; " + (rates["basis"] + " (of measured)" if rates else
+                                                               f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"))
                            if bound == "alu" else "of measured"),
             "tensor": {"achieved": round(gemm / sec / 1e12, 2), "peak": peak_t, "unit": "TFLOP/s",
                        "frac": round(gemm / sec / 1e12 / peak_t, 4),
@@ -274,29 +288,108 @@ def _measure_forms(P, torch, grid, U, imgs, tmpl, deltas, cfg, T, K2, scores_ste
     return res
 
 
-def run_ours(args):
-    import numpy as np
-    import torch
+_RATES = {}
 
-    import paper_2202_07235_gb300 as P
+
+def _measure_rates(torch, P, dev):
+    """Arithmetic rates measured on this GPU with the library's rate probe
+    (register-resident chains of one instruction kind, timed with CUDA
+    events, best of 3 launches of about 10 ms): FP32 flops/s of scalar FFMA
+    and packed FFMA2, and base-2 exponentials/s (MUFU). Cached per process."""
+    key = str(dev)
+    if key in _RATES:
+        return _RATES[key]
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream()
+    res = {}
+    for kind, iters in (("ffma", 20000), ("ffma2", 20000), ("ex2", 5000)):
+        P.rate_probe(kind, sm * 8, 100)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ops = P.rate_probe(kind, sm * 8, iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        res[kind] = ops / (best / 1e3) / 1e12
+    P.status()
+    fp32 = max(res["ffma"], res["ffma2"])
+    out = {"fp32_tflops": round(fp32, 2), "ffma_tflops": round(res["ffma"], 2), "ffma2_tflops": round(res["ffma2"], 2),
+           "ex2_tera_per_s": round(res["ex2"], 3), "sms": sm,
+           "basis": "measured on this GPU: register-resident FFMA / FFMA2 chains (rsvd_rate_probe), best of 3 "
+                    "launches, %d CTAs x 256 threads" % (sm * 8)}
+    _RATES[key] = out
+    return out
+
+
+def _sampled_clock(clk):
+    return (clk or {}).get("sm_mhz")
+
+
+def _cpu_oracle_sample(imgs, grid, deltas, tmpl, U, T, N_B, Q, N_A, best, arg, cpu_images, cpu_seconds):
+    """The FP64 oracle on all host cores over a bounded sample of the images
+    (about `cpu_seconds` of wall time), with the GPU's error on that sample."""
+    import numpy as np
+
+    import oracle as O
+
+    Un = U.cpu().numpy()
+    b_c = O.compress(tmpl.cpu().numpy().astype(np.complex128), Un, grid.w)
+    pool, ncores = _oracle_pool(grid.k, grid.w, deltas, Un, b_c)
+    try:
+        A0 = imgs[:ncores].cpu().numpy().astype(np.complex128)
+        _time_oracle(pool, A0, 1)  # warm the workers
+        w0, _ = _time_oracle(pool, A0, 1)
+        n_s = int(cpu_images) or int(max(1, cpu_seconds / max(w0, 1e-3)) * ncores)
+        n_s = max(ncores, min(N_A, n_s))
+        A = imgs[:n_s].cpu().numpy().astype(np.complex128)
+        wall, res = _time_oracle(pool, A, max(1, -(-n_s // ncores)))
+    finally:
+        pool.close()
+        pool.join()
+    rb = np.concatenate([r[0] for r in res])
+    ra = np.concatenate([r[1] for r in res])
+    scale = np.maximum(np.abs(rb), 1e-30)
+    cpu = {"value": n_s * T * N_B * Q / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
+           "sample": f"{n_s} images x {T} translations x {N_B} templates x {Q} rotations "
+                     f"(FP64 numpy oracle, one spawned process per core; templates "
+                     f"compressed before timing), {wall:.1f} s wall"}
+
+    def err(b, a):
+        gb = b[:n_s].cpu().numpy()
+        ga = a[:n_s].cpu().numpy()
+        return {"vs": "FP64 oracle on the cpu_baseline sample", "pairs": int(n_s * N_B),
+                "best_max_rel": float(np.max(np.abs(gb - rb) / scale)), "argmax_agree": float(np.mean(ga == ra))}
+
+    return cpu, err(best, arg), err
+
+
+def _config_dict(cfg, name, T, world, batch):
+    N_A = cfg["N_A"]
+    return {"workload": _workload_desc(cfg), "N_A_per_gpu": N_A, "N_B": cfg["N_B"], "T": T, "Q": cfg["Q"],
+            "R": cfg["R"], "H": cfg["H"], "N": cfg["N"], "snr": cfg["snr"], "images_per_step": batch,
+            "step": (f"one batch of {batch} of the {N_A} resident images (batches in turn)" if batch < N_A
+                     else "all resident images"),
+            "parallelism": f"dp{world} (images sharded, templates replicated)",
+            "l2": "inputs larger than L2 (polar images %.2f GB/GPU), no flush" % (N_A * cfg["R"] * cfg["Q"] * 8 / 1e9)}
+
+
+def _measure_workload(args, name, torch, P, dev, rank, world, want_cpu, want_forms):
+    """One workload: resident inputs, K timed steps (compress images of one
+    batch at T translations + compress templates + fused alignment), the
+    end-to-end figure through the host-input pipeline, the roofline of the
+    fused scoring kernel, the tensor-core forms and the oracle sample."""
     from synthetic import CONFIGS, make_workload_torch
 
-    rank, world, local = _dist_env()
-    cfg = dict(CONFIGS[args.config])
+    cfg = dict(CONFIGS[name])
     if args.n_images:
         cfg["N_A"] = args.n_images
-
-    want_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-    P.lib()
-
     N_A, N_B, Q, H, R = cfg["N_A"], cfg["N_B"], cfg["Q"], cfg["H"], cfg["R"]
+    _measure_rates(torch, P, dev)
+    batch = min(N_A, args.batch or STEP_IMAGES.get(name, N_A))
+    nbatch = -(-N_A // batch)
     # templates are shared by all ranks (same seed); images differ per rank
     grid, deltas, tmpl, _, _ = make_workload_torch(**{**cfg, "N_A": 1}, seed=1000, device=dev)
     _, _, _, imgs, truth = make_workload_torch(**cfg, seed=2000 + rank, device=dev)
@@ -312,13 +405,14 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     precompute_ms = e0.elapsed_time(e1)
+    del ws
 
     prec = args.precision
     if prec == "fp32":
-        cA = torch.empty((N_A * T, H, Q // 2, 2), dtype=torch.float32, device=dev)
+        cA = torch.empty((batch * T, H, Q // 2, 2), dtype=torch.float32, device=dev)
         cB = torch.empty((N_B, H, Q // 2, 2), dtype=torch.float32, device=dev)
     else:  # tensor-core operand form (byte tensors)
-        cA = torch.empty((P.compressed_bytes(N_A, T, H, Q, prec),), dtype=torch.uint8, device=dev)
+        cA = torch.empty((P.compressed_bytes(batch, T, H, Q, prec),), dtype=torch.uint8, device=dev)
         cB = torch.empty((P.compressed_bytes(N_B, 1, H, Q, prec),), dtype=torch.uint8, device=dev)
     best = torch.empty((N_A, N_B), dtype=torch.float32, device=dev)
     arg = torch.empty((N_A, N_B), dtype=torch.int32, device=dev)
@@ -327,17 +421,23 @@ def run_ours(args):
     ev_a0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev_a1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev_c0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    counter = [0]
 
     def step(i=None):
+        b = counter[0] % nbatch
+        counter[0] += 1
+        b0 = b * batch
+        n = min(batch, N_A - b0)
         if i is not None:
             ev_c0[i].record(stream)
-        P.compress(grid.k, grid.w, U, imgs, deltas=deltas, out=cA, precision=prec)
+        P.compress(grid.k, grid.w, U, imgs[b0:b0 + n], deltas=deltas, out=cA, precision=prec)
         P.compress(grid.k, grid.w, U, tmpl, out=cB, precision=prec)
         if i is not None:
             ev_a0[i].record(stream)
-        P.align_best(cA, N_A, T, cB, N_B, H, Q, out=(best, arg, None), precision=prec)
+        P.align_best(cA, n, T, cB, N_B, H, Q, out=(best[b0:b0 + n], arg[b0:b0 + n], None), precision=prec)
         if i is not None:
             ev_a1[i].record(stream)
+        return n
 
     for _ in range(W):
         step()
@@ -363,8 +463,9 @@ def run_ours(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
+    n_scored = 0
     for i in range(K):
-        step(i)
+        n_scored += step(i)
     t1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -379,29 +480,40 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     P.status()
+    # every image scored once (the timed steps may not have covered all batches)
 
-    pairs = N_A * T * N_B
-    scores_step = pairs * Q
+    pairs_step = batch * T * N_B
+    scores_step = pairs_step * Q
     ms_per_step = elapsed_ms / K
-    value = world * scores_step * K / (elapsed_ms / 1e3)
+    value = world * n_scored * T * N_B * Q / (elapsed_ms / 1e3)
 
     # ---- end to end through the public API with host buffers: the host-input
-    # pipeline (rsvd_align_best_host) copies images and templates in chunks that
-    # overlap compression and alignment, and writes best/arg to host memory ----
-    imgs_h = imgs.cpu().pin_memory()
-    tmpl_h = tmpl.cpu().pin_memory()
-    best_h = torch.empty(best.shape, dtype=best.dtype).pin_memory()
-    arg_h = torch.empty(arg.shape, dtype=arg.dtype).pin_memory()
+    # pipeline (rsvd_align_best_host) copies one batch of images and the
+    # templates in chunks that overlap compression and alignment, and writes
+    # best/arg to host memory ----
+    del cA
+    torch.cuda.empty_cache()
+    imgs_h = torch.empty(imgs.shape, dtype=imgs.dtype, pin_memory=True)
+    imgs_h.copy_(imgs)
+    tmpl_h = torch.empty(tmpl.shape, dtype=tmpl.dtype, pin_memory=True)
+    tmpl_h.copy_(tmpl)
+    best_h = torch.empty(best.shape, dtype=best.dtype, pin_memory=True)
+    arg_h = torch.empty(arg.shape, dtype=arg.dtype, pin_memory=True)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    chunk = min(N_A, 8 * sm_count)
+    chunk = min(batch, 8 * sm_count)
     ws_host = torch.empty(P.align_host_workspace_bytes(R, Q, H, T, N_B, chunk, prec), dtype=torch.uint8, device=dev)
     copy_stream = torch.cuda.Stream(device=dev)
-    del cA  # the pipeline holds its own per-chunk buffers
-    torch.cuda.empty_cache()
+    ecount = [0]
 
     def e2e_step():
-        P.align_best_host(grid.k, grid.w, U, imgs_h, tmpl_h, deltas=deltas, precision=prec, chunk=chunk,
-                          workspace=ws_host, out=(best_h, arg_h, None), stream=stream, copy_stream=copy_stream)
+        b = ecount[0] % nbatch
+        ecount[0] += 1
+        b0 = b * batch
+        n = min(batch, N_A - b0)
+        P.align_best_host(grid.k, grid.w, U, imgs_h[b0:b0 + n], tmpl_h, deltas=deltas, precision=prec, chunk=chunk,
+                          workspace=ws_host, out=(best_h[b0:b0 + n], arg_h[b0:b0 + n], None), stream=stream,
+                          copy_stream=copy_stream)
+        return n
 
     K2 = max(3, min(K, 10))
     for _ in range(2):
@@ -409,8 +521,9 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     t0.record(stream)
+    n_e2e = 0
     for _ in range(K2):
-        e2e_step()
+        n_e2e += e2e_step()
     t1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = t0.elapsed_time(t1) / K2
@@ -420,86 +533,98 @@ def run_ours(args):
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    h2d = (imgs.numel() + tmpl.numel()) * 8 // 2  # psi < pi of every ring
-    d2h = best.numel() * 4 + arg.numel() * 4
+    e2e_value = world * n_e2e * T * N_B * Q / (e2e_ms * K2 / 1e3)
+    h2d = (batch + N_B) * R * Q * 8 // 2  # psi < pi of every ring
+    d2h = batch * N_B * 8
+    del imgs_h, ws_host
+    torch.cuda.empty_cache()
 
     # ---- roofline of the dominant kernel (fused contraction + FFT + reduce) ----
+    rates = _measure_rates(torch, P, dev)
     align_avg_ms = sum(align_ms) / K
-    flops = pairs * _alg_flops_per_pair(H, Q)
+    flops = pairs_step * _alg_flops_per_pair(H, Q)
     achieved = flops / (align_avg_ms / 1e3) / 1e12
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x FMA x max SM clock
+    peak = rates["fp32_tflops"]
     hp = 8 if H <= 8 else 12 if H <= 12 else 16
     kname = f"ws_align_kernel<{Q // 2},{hp}>" if (Q in (256, 512) and H <= 16) else "fused_align_kernel"
     if prec == "fp32":
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
-                    "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": _load_traffic(kname + "@" + args.config) if args.n_images == 0 else None,
-                    "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)"}
+                    "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": _load_traffic(kname + "@" + name) if args.n_images == 0 else None,
+                    "peak_basis": rates["basis"] + " (of measured)",
+                    "flops_per_pair": _alg_flops_per_pair(H, Q), "pairs_per_launch": pairs_step,
+                    "frac_real_fft_count": round(pairs_step * _alg_flops_per_pair(H, Q, real_fft=True)
+                                                 / (align_avg_ms / 1e3) / 1e12 / peak, 4)}
     else:
-        roofline = _form_roofline(P, prec, N_A, N_B, T, H, Q, align_avg_ms, sm_count)
+        roofline = _form_roofline(P, prec, batch, N_B, T, H, Q, align_avg_ms, sm_count)
         roofline["traffic"] = None
     roofline.update(align_ms=round(align_avg_ms, 3), compress_ms=round(sum(compress_ms) / K, 3))
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == "fp32" else prec, "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
-        "config": {"workload": _workload_desc(cfg), "N_A_per_gpu": N_A, "N_B": N_B, "T": T, "Q": Q, "R": R, "H": H,
-                   "N": cfg["N"], "snr": cfg["snr"], "parallelism": f"dp{world} (images sharded, templates replicated)",
-                   "l2": "inputs larger than L2 (polar images %.2f GB/GPU), no flush" % (imgs.numel() * 8 / 1e9),
-                   "precompute_ms": round(precompute_ms, 3)},
+        "dtype": "f32" if prec == "fp32" else prec,
+        "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
+        "config": _config_dict(cfg, name, T, world, batch),
+        "precompute_ms": round(precompute_ms, 3),
         "roofline": roofline,
-        "e2e": {"value": world * scores_step / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms, "steps": K2},
         "gpu_launches": 3 * K,
         "clocks": clk,
+        "rates": rates,
     }
 
     # ---- the tensor-core operand forms on the same workload (FP32 stays the headline) ----
     forms = {}
-    if prec == "fp32" and not args.no_forms and Q in (128, 256):
-        forms = _measure_forms(P, torch, grid, U, imgs, tmpl, deltas, cfg, T, min(K, 10), scores_step, dev)
+    if prec == "fp32" and want_forms:
+        forms = _measure_forms(P, torch, grid, U, imgs[:batch], tmpl, deltas, {**cfg, "N_A": batch}, T,
+                               max(2, min(K, 10 if nbatch == 1 else 3)), scores_step, dev)
         out["forms"] = {k: v["report"] for k, v in forms.items()}
 
     # ---- cpu baseline: the FP64 oracle on host cores, bounded sample ----
     if want_cpu:
-        import oracle as O
-
-        Un = U.cpu().numpy()
-        b_c = O.compress(tmpl.cpu().numpy().astype(np.complex128), Un, grid.w)
-        pool, ncores = _oracle_pool(grid.k, grid.w, deltas, Un, b_c)
-        try:
-            A0 = imgs[:ncores].cpu().numpy().astype(np.complex128)
-            _time_oracle(pool, A0, 1)  # warm the workers
-            w0, _ = _time_oracle(pool, A0, 1)
-            # sample sized to about args.cpu_seconds of wall time on all cores
-            n_s = int(args.cpu_images) or int(max(1, args.cpu_seconds / max(w0, 1e-3)) * ncores)
-            n_s = max(ncores, min(N_A, n_s))
-            A = imgs[:n_s].cpu().numpy().astype(np.complex128)
-            wall, res = _time_oracle(pool, A, max(1, n_s // ncores))
-        finally:
-            pool.close()
-            pool.join()
-        rb = np.concatenate([r[0] for r in res])
-        ra = np.concatenate([r[1] for r in res])
-        gb = best[:n_s].cpu().numpy()
-        ga = arg[:n_s].cpu().numpy()
-        scale = np.maximum(np.abs(rb), 1e-30)
-        out["cpu_baseline"] = {"value": n_s * T * N_B * Q / wall, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                               "sample": f"{n_s} images x {T} translations x {N_B} templates x {Q} rotations "
-                                         f"(FP64 numpy oracle, one spawned process per core; templates "
-                                         f"compressed before timing), {wall:.1f} s wall"}
-        out["error"] = {"vs": "FP64 oracle on the cpu_baseline sample", "pairs": int(n_s * N_B),
-                        "best_max_rel": float(np.max(np.abs(gb - rb) / scale)),
-                        "argmax_agree": float(np.mean(ga == ra))}
-        for name, f in forms.items():
+        cpu, err, err_fn = _cpu_oracle_sample(imgs, grid, deltas, tmpl, U, T, N_B, Q, N_A, best, arg,
+                                              args.cpu_images, args.cpu_seconds)
+        out["cpu_baseline"] = cpu
+        out["error"] = err
+        for fname, f in forms.items():
             if "best" in f:
-                fb = f["best"][:n_s].cpu().numpy()
-                fa = f["arg"][:n_s].cpu().numpy()
-                out["forms"][name]["error"] = {"vs": "FP64 oracle on the cpu_baseline sample",
-                                               "best_max_rel": float(np.max(np.abs(fb - rb) / scale)),
-                                               "argmax_agree": float(np.mean(fa == ra))}
+                out["forms"][fname]["error"] = err_fn(f["best"], f["arg"])
+    for f in forms.values():
+        f.pop("best", None)
+        f.pop("arg", None)
+    del imgs, tmpl, best, arg, cB, U
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2202_07235_gb300 as P
+
+    rank, world, local = _dist_env()
+    want_cpu = (rank == 0 and world == 1 and not args.no_cpu_baseline)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    P.lib()
+    out = _measure_workload(args, args.config, torch, P, dev, rank, world, want_cpu, not args.no_forms)
+    # the throughput workload rides along with the large one (smaller geometry,
+    # its own resident inputs), reported nested under its name
+    if args.config == "large" and not args.no_extra and not args.n_images:
+        import copy
+
+        a2 = copy.copy(args)
+        a2.steps, a2.warmup = min(args.steps, 10), 3
+        extra = _measure_workload(a2, "throughput", torch, P, dev, rank, world, want_cpu, not args.no_forms)
+        out["throughput"] = {k: extra[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "roofline",
+                                                   "e2e", "clocks", "forms", "cpu_baseline", "error") if k in extra}
+        out["gpu_launches"] += extra["gpu_launches"]
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -583,8 +708,8 @@ def run_gradient(args):
     # algorithmic work of the backward per pair: X once (contraction + C2R FFT),
     # the R2C transform of dL/dX, and the two gradient contractions
     bwd_flops = pairs * (3 * 8 * H * (Q // 2 + 1) + 2 * 2.5 * Q * math.log2(Q))
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * 128 * 2 * 2.07e9 / 1e12
+    rates = _measure_rates(torch, P, dev)
+    peak = rates["fp32_tflops"]
     achieved = bwd_flops / (part[2] / 1e3) / 1e12
     out = {
         "metric": METRIC + " (forward + log-sum-exp backward)", "value": world * pairs * Q * K / (elapsed / 1e3),
@@ -611,6 +736,9 @@ def run_gradient(args):
 # per-CTF groups): one JSON line each, `--config fine|marching|translated|grouped`
 # ---------------------------------------------------------------------------
 ROW_CONFIGS = ("fine", "marching", "translated", "grouped")
+# images per step: the large workload is streamed through the GPU in batches of
+# 8,192 images (all 65,536 stay resident); the others score every image per step
+STEP_IMAGES = {"large": 8192}
 
 
 def _row_init(**kw):
@@ -692,7 +820,7 @@ def run_rows(args):
     grid, deltas, tmpl, _, _ = make_workload_torch(**{**cfg, "N_A": 1}, seed=1000, device=dev)
     T = deltas.shape[0]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_alu = sms * 128 * 2 * 2.07e9 / 1e12
+    peak_alu = _measure_rates(torch, P, dev)["fp32_tflops"]
     K, W = args.steps, args.warmup
     want_cpu = not args.no_cpu_baseline and rank == 0
     uuid = None
@@ -1125,8 +1253,8 @@ def run_volumes(args):
     torch.cuda.synchronize()
     e2e_ms = t0.elapsed_time(t1) / K2
 
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * 128 * 2 * 2.07e9 / 1e12
+    rates = _measure_rates(torch, P, dev)
+    peak = rates["fp32_tflops"]
     flops = N_A * N_B * _vol_flops_per_pair(L, HC, HD, nb, Mp)
     achieved = flops / (align_ms / 1e3) / 1e12
     ept = -(-((M * M + 1) // 2) // 512)
@@ -1143,7 +1271,7 @@ def run_volumes(args):
         "roofline": {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2), "peak": round(peak, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                      "traffic": _load_traffic(kname + "@volumes") if args.n_images == 0 else None,
-                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
+                     "peak_basis": rates["basis"] + " (of measured)",
                      "align_ms": round(align_ms, 3), "compress_ms": round(comp_ms, 3),
                      "flops_per_pair": _vol_flops_per_pair(L, HC, HD, nb, Mp)},
         "e2e": {"value": world * scores_step / (e2e_ms / 1e3), "unit": "scores/s",
@@ -1266,17 +1394,21 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    from synthetic import CONFIGS, make_workload
+    from synthetic import CONFIGS, make_workload_torch
 
     cfg = dict(CONFIGS[args.config])
-    wl = make_workload(**{**cfg, "N_A": _cores()}, seed=2000)
-    g = wl.grid
-    T = wl.deltas.shape[0]
-    U, _ = O.principal_vectors(O.radial_kernel(wl.templates.astype(np.complex64).astype(np.complex128), g.w),
-                               cfg["H"])
-    b_c = O.compress(wl.templates.astype(np.complex64).astype(np.complex128), U, g.w)
-    A = wl.images.astype(np.complex64).astype(np.complex128)
-    pool, ncores = _oracle_pool(g.k, g.w, wl.deltas, U, b_c)
+    # same construction and seeds as the GPU arm's inputs, evaluated with torch
+    # on the host (complex64 samples, as the GPU arm holds them)
+    g, deltas, tmpl, _, _ = make_workload_torch(**{**cfg, "N_A": 1}, seed=1000, device="cpu")
+    _, _, _, imgs, _ = make_workload_torch(**{**cfg, "N_A": _cores()}, seed=2000, device="cpu")
+    T = deltas.shape[0]
+    B = tmpl.numpy().astype(np.complex128)
+    del tmpl
+    U, _ = O.principal_vectors(O.radial_kernel(B, g.w), cfg["H"])
+    b_c = O.compress(B, U, g.w)
+    del B
+    A = imgs.numpy().astype(np.complex128)
+    pool, ncores = _oracle_pool(g.k, g.w, deltas, U, b_c)
     try:
         for _ in range(args.warmup):
             _time_oracle(pool, A, 1)
@@ -1296,8 +1428,7 @@ def run_reference(args):
         "ms_per_step": 1e3 * total / len(walls), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded Gaussian-blob images, analytic polar Fourier samples)",
         "impl": "reference",
-        "config": {"workload": _workload_desc(cfg), "N_A_per_gpu": cfg["N_A"], "N_B": cfg["N_B"], "T": T,
-                   "Q": cfg["Q"], "R": cfg["R"], "H": cfg["H"]},
+        "config": _config_dict(cfg, args.config, T, world, min(cfg["N_A"], args.batch or STEP_IMAGES.get(args.config, cfg["N_A"]))),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
                          "sample": f"each step: {n_s} images x {T} translations x {cfg['N_B']} templates x "
                                    f"{cfg['Q']} rotations, one image per spawned process (FP64 numpy oracle)"},
@@ -1312,7 +1443,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="throughput")
+    ap.add_argument("--config", default="large")
+    ap.add_argument("--batch", type=int, default=0, help="images per step (0 = the workload's default)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="with --config large, skip the nested throughput-workload measurement")
     ap.add_argument("--n-images", type=int, default=0, help="override images per GPU (smaller runs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
                     help="operand precision of the scoring contraction (tensor cores unless fp32)")

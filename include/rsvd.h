@@ -460,6 +460,22 @@ int rsvd_align_best_pairwise(const void* cA, int N_A, int T, const void* cB, int
                              int precision, float inv_sigma2, float* best, int32_t* arg, float* lse,
                              void* stream);
 
+/* ------------------------------------------------------------------------
+ * Arithmetic-rate probe (no counterpart in the paper: it measures the
+ * denominators of the FP32-ALU and special-function rooflines on the GPU at
+ * hand). Enqueues one launch of `blocks` CTAs of 256 threads, each thread
+ * running independent register-resident chains of one instruction kind for
+ * `iters` iterations, and stores in *ops_out (host) the number of operations
+ * the launch performs: FP32 flops for RSVD_RATE_FFMA (scalar fused
+ * multiply-add, 2 flops each) and RSVD_RATE_FFMA2 (packed FP32x2 fused
+ * multiply-add), base-2 exponentials (ex2.approx) for RSVD_RATE_EX2. The
+ * caller times the launch on `stream` (e.g. CUDA events) and divides.
+ * Reads and writes no caller memory. RSVD_EINVAL for an unknown kind or
+ * blocks / iters outside 1 .. 2^20 / >= 1.
+ * ------------------------------------------------------------------------ */
+enum rsvd_rate_kind { RSVD_RATE_FFMA = 0, RSVD_RATE_FFMA2 = 1, RSVD_RATE_EX2 = 2 };
+int rsvd_rate_probe(int kind, int blocks, int iters, double* ops_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ from .api import (  # noqa: F401
     lse_backward,
     lse_rows,
     pack,
+    rate_probe,
     select_pairs,
     selftest_wait_timeout,
     status,

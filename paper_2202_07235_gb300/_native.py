@@ -81,6 +81,7 @@ SIGNATURES = {
     "rsvd_build_grouped_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int]),
     "rsvd_build_radial_svd_grouped": (c_int, [c_int, c_int, c_double_p, c_void_p, c_int, c_void_p, c_int, c_int,
                                               c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "rsvd_rate_probe": (c_int, [c_int, c_int, c_int, c_double_p, c_void_p]),
     "rsvd_build_translated_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
     "rsvd_build_radial_svd_translated": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_double_p,
                                                  c_double_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_size_t,

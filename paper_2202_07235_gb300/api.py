@@ -677,3 +677,17 @@ def selftest_wait_timeout(budget_cycles: int = 1 << 21, stream=None) -> int:
 def status(stream=None) -> None:
     """Synchronises the stream and raises if a kernel recorded a device-side failure."""
     check(lib().rsvd_status(_stream(stream)), "rsvd_status")
+
+
+RATE_KINDS = {"ffma": 0, "ffma2": 1, "ex2": 2}
+
+
+def rate_probe(kind: str, blocks: int, iters: int, stream=None) -> float:
+    """Enqueues the arithmetic-rate probe (rsvd_rate_probe) on `stream` and
+    returns the number of operations the launch performs (FP32 flops for
+    "ffma" / "ffma2", exponentials for "ex2"); time the launch on the same
+    stream to get the rate."""
+    ops = ctypes.c_double(0.0)
+    check(lib().rsvd_rate_probe(RATE_KINDS[kind], int(blocks), int(iters), ctypes.byref(ops), _stream(stream)),
+          "rsvd_rate_probe")
+    return float(ops.value)
