@@ -22,10 +22,15 @@
 
 namespace rsvd {
 
-// S = 128: 256 contraction + 256 FFT threads, 3 image rows per thread (H <= 12).
-// S = 256: one template (H <= 16) takes 32 KB of shared memory, so a batch holds
-// two; 4 image rows per contraction thread (the 384-thread block leaves 168
-// registers per thread) make 8 pairs per batch, the work of 128 FFT threads.
+// S = 128: 256 contraction + 256 FFT threads, 3 image rows per thread (H <= 12);
+// a batch of TB templates is one bulk copy.
+// S = 256: 256 contraction threads keep 4 image rows x HP components each in
+// registers and 256 FFT threads (16 lanes per pair) take 16 pairs per batch,
+// i.e. TB = 4 templates. One template at H = 16 takes 32 KB of shared memory,
+// so a batch arrives as SUB = 2 copies of TBL = 2 templates through a double
+// buffer. The 512-thread block starts at 128 registers per thread; the
+// contraction warps raise theirs to 168 and the FFT warps lower theirs to 88
+// (setmaxnreg; 256 x 168 + 256 x 88 = the block's 65,536).
 template <int S, int HP>
 struct WsCfg {
   static constexpr int P1 = FftSplit<S>::P1, P2 = FftSplit<S>::P2, F = P2, RR = P1 / P2;
@@ -33,7 +38,7 @@ struct WsCfg {
   static constexpr int RT = kWide ? cmax(1, cmin(4, 64 / HP)) : cmax(1, cmin(4, 36 / HP));  // rows per thread
   static constexpr int GC = cmax(1, 256 / S);            // contraction row groups
   static constexpr int CT = GC * S;                      // contraction threads
-  static constexpr int FT = kWide ? 128 : 256;           // FFT threads
+  static constexpr int FT = 256;                         // FFT threads
   static constexpr int NT = CT + FT;
   static constexpr int RP = GC * RT;                     // rows per pass
   static constexpr int PGF = FT / F;                     // pairs per FFT round
@@ -41,12 +46,21 @@ struct WsCfg {
   static constexpr int SP = pair_stride(S, P1, P2);
   static constexpr int PER_TB = 2 * HP * S * 8 + 2 * RP * SP * 8 + 24 * RP;
   static constexpr int TB_SMEM = (200 * 1024 - 2 * S * 8 - 64) / PER_TB;
-  static constexpr int TB = cmax(1, cmin(TB_SMEM, cmax(1, PGF / RP)));  // templates per batch
+  // templates per batch (FFT hand-off); per bulk copy (TBL, SUB copies per batch)
+  static constexpr int TB = kWide ? cmax(1, PGF / RP) : cmax(1, cmin(TB_SMEM, cmax(1, PGF / RP)));
+  static constexpr int TBL_SMEM = (224 * 1024 - 2 * S * 8 - 64 - 2 * TB * RP * SP * 8 - 24 * RP * TB) /
+                                  (2 * HP * S * 8);
+  static constexpr int TBL = kWide ? (TBL_SMEM >= TB ? TB : TBL_SMEM >= TB / 2 ? TB / 2 : 1) : TB;
+  static constexpr int SUB = TB / TBL;
   static constexpr int PAIRS = RP * TB;
   static constexpr int SPB = PAIRS + (PGF - PAIRS % PGF) % PGF;  // pair regions per buffer (incl. dummies)
-  static constexpr size_t SMEM = (size_t)2 * TB * HP * S * 8 + (size_t)2 * SPB * SP * 8 + (size_t)2 * S * 8 +
+  static constexpr size_t SMEM = (size_t)2 * TBL * HP * S * 8 + (size_t)2 * SPB * SP * 8 + (size_t)2 * S * 8 +
                                  (size_t)2 * 3 * PAIRS * 4 + 64;
-  static constexpr bool kFits = SMEM <= 227 * 1024 && S <= 256 && TB_SMEM >= 1;
+  // register split between the roles (kWide): 256 x (kRegC + kRegF) = 65,536
+  static constexpr bool kRegSplit = kWide;
+  static constexpr int kRegC = 168, kRegF = 88;
+  static constexpr bool kFits = SMEM <= 227 * 1024 && S <= 256 && TBL >= 1 && TB % TBL == 0 &&
+                                (!kRegSplit || (CT == 256 && FT == 256));
 };
 
 // clock budget of one bounded wait (about half a second at 2 GHz)
@@ -59,12 +73,12 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
   using C = WsCfg<S, HP>;
   constexpr int M = S, Q = 2 * S, P1 = C::P1, P2 = C::P2, RP = C::RP, RT = C::RT, TB = C::TB;
   constexpr int CT = C::CT, FT = C::FT, NT = C::NT, SP = C::SP, XP = C::XP, F = C::F, RR = C::RR;
-  constexpr int PAIRS = C::PAIRS, PGF = C::PGF;
+  constexpr int PAIRS = C::PAIRS, PGF = C::PGF, TBL = C::TBL, SUB = C::SUB;
   static_assert(P1 * P2 == M && P1 % P2 == 0 && 32 % F == 0, "bad FFT split");
 
   extern __shared__ __align__(128) unsigned char ws_smem[];
-  float2* tbuf = reinterpret_cast<float2*>(ws_smem);   // [2][TB][HP][S], rows h >= H zero
-  float2* spec = tbuf + 2 * TB * HP * S;               // [2][SPB][SP] (PAIRS pairs + dummy regions)
+  float2* tbuf = reinterpret_cast<float2*>(ws_smem);   // [2][TBL][HP][S], rows h >= H zero
+  float2* spec = tbuf + 2 * TBL * HP * S;              // [2][SPB][SP] (PAIRS pairs + dummy regions)
   float2* twQ = spec + 2 * C::SPB * SP;                 // [M]
   float2* tw1 = twQ + M;                               // [M]
   float* res = reinterpret_cast<float*>(tw1 + M);      // [2][3][PAIRS]
@@ -89,7 +103,7 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
     sincospif(-2.0f * (float)(t * k1) / (float)M, &sn, &cs);
     tw1[i] = make_float2(cs, sn);
   }
-  for (int i = tid; i < 2 * TB * (HP - H) * S; i += NT) {
+  for (int i = tid; i < 2 * TBL * (HP - H) * S; i += NT) {
     const int slot = i / ((HP - H) * S), rem = i % ((HP - H) * S);
     tbuf[(size_t)slot * HP * S + (size_t)H * S + rem] = make_float2(0.f, 0.f);
   }
@@ -104,35 +118,40 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
   const int nbatch = (N_B + TB - 1) / TB;
   const int passes = (rows_cta + RP - 1) / RP;
   const int total = passes * nbatch;
+  // template copies: TBL templates each, nsubp per pass (the last batch of a
+  // pass may need fewer than SUB); copy L holds templates (L % nsubp) * TBL + ..
+  const int nsubp = (N_B + TBL - 1) / TBL;
+  const long long total_loads = (long long)passes * nsubp;
 
   if (tid < CT) {
     // ======================= contraction warps =======================
+    if constexpr (C::kRegSplit) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(C::kRegC));
     const int g = tid / S, s = tid % S;
     const bool slot0 = (s == 0);
-    auto issue = [&](int it) {
-      const int b = it % nbatch;
-      const int j0 = b * TB;
-      const int nb = min(TB, N_B - j0);
-      const int buf = it & 1;
+    auto issue = [&](long long L) {
+      const int j0 = (int)(L % nsubp) * TBL;
+      const int nb = min(TBL, N_B - j0);
+      const int buf = (int)(L & 1);
       const uint32_t per = (uint32_t)H * S * 8;
       mbar_arrive_expect_tx(&mbar[buf], per * nb);
       if (HP == H) {
-        bulk_g2s(tbuf + (size_t)buf * TB * HP * S, p.cB + (size_t)j0 * H * S, per * nb, &mbar[buf]);
+        bulk_g2s(tbuf + (size_t)buf * TBL * HP * S, p.cB + (size_t)j0 * H * S, per * nb, &mbar[buf]);
       } else {
         for (int jj = 0; jj < nb; ++jj)
-          bulk_g2s(tbuf + (size_t)(buf * TB + jj) * HP * S, p.cB + (size_t)(j0 + jj) * H * S, per, &mbar[buf]);
+          bulk_g2s(tbuf + (size_t)(buf * TBL + jj) * HP * S, p.cB + (size_t)(j0 + jj) * H * S, per, &mbar[buf]);
       }
     };
-    if (tid == 0 && total > 0) issue(0);
-    int waited_upto = -1;  // iterations whose copies this thread has seen complete
+    if (tid == 0) {
+      if (total_loads > 0) issue(0);
+      if (total_loads > 1) issue(1);
+    }
+    long long waited_upto = -1;  // copies this thread has seen complete
+    long long issued_upto = total_loads < 2 ? total_loads - 1 : 1;
     float2 a[RT][HP];
     for (int it = 0; it < total; ++it) {
-      const int ps = (it / nbatch) * RP;
+      const int pass = it / nbatch;
+      const int ps = pass * RP;
       const int b = it % nbatch;
-      const int nb = min(TB, N_B - b * TB);
-      named_sync(kBarCW, CT);  // every contraction thread is done with iteration it-1
-      const bool aborted = *reinterpret_cast<volatile int*>(abort_flag) != 0;
-      if (tid == 0 && it + 1 < total && !aborted) issue(it + 1);
       if (b == 0) {
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
@@ -146,61 +165,67 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
           }
         }
       }
-      if (!aborted) {
-        if (mbar_wait_bounded(&mbar[it & 1], (it >> 1) & 1, kWaitBudget)) {
-          waited_upto = it;
-        } else {
-          record(p.status, kDevTimeout);
-          atomicExch(abort_flag, 1);
-        }
-      }
       if (it >= 2) named_sync(kBarFree0 + (it & 1), CT + FT);
-      const float2* tb = tbuf + (size_t)(it & 1) * TB * HP * S + s;
       float2* sp = spec + (size_t)(it & 1) * C::SPB * SP;
 #pragma unroll 1
-      for (int jj = 0; jj < TB; ++jj) {
-        if (jj < nb) {
-          // (P, Qa) = sum_h (a.x b.x, a.y b.y), (Ra, Sa) = sum_h (a.x b.y, a.y b.x): two packed
-          // FP32x2 FMAs per row and h; the swapped template value is shared by the RT rows
-          float2 PQ[RT], RS[RT];
+      for (int u = 0; u < SUB; ++u) {
+        const int jb = b * TB + u * TBL;  // first template of this copy
+        if (jb >= N_B) break;
+        const long long L = (long long)pass * nsubp + b * SUB + u;
+        const int nb = min(TBL, N_B - jb);
+        if (*reinterpret_cast<volatile int*>(abort_flag) == 0) {
+          if (mbar_wait_bounded(&mbar[L & 1], (uint32_t)((L >> 1) & 1), kWaitBudget)) {
+            waited_upto = L;
+          } else {
+            record(p.status, kDevTimeout);
+            atomicExch(abort_flag, 1);
+          }
+        }
+        const float2* tb = tbuf + (size_t)(L & 1) * TBL * HP * S + s;
+#pragma unroll 1
+        for (int jj = 0; jj < TBL; ++jj) {
+          if (jj < nb) {
+            // (P, Qa) = sum_h (a.x b.x, a.y b.y), (Ra, Sa) = sum_h (a.x b.y, a.y b.x): two packed
+            // FP32x2 FMAs per row and h; the swapped template value is shared by the RT rows
+            float2 PQ[RT], RS[RT];
 #pragma unroll
-          for (int i = 0; i < RT; ++i) PQ[i] = RS[i] = make_float2(0.f, 0.f);
-          const float2* bp = tb + (size_t)jj * HP * S;
+            for (int i = 0; i < RT; ++i) PQ[i] = RS[i] = make_float2(0.f, 0.f);
+            const float2* bp = tb + (size_t)jj * HP * S;
 #pragma unroll
-          for (int h = 0; h < HP; ++h) {
-            const float2 bv = bp[h * S];
-            const float2 bs = make_float2(bv.y, bv.x);
+            for (int h = 0; h < HP; ++h) {
+              const float2 bv = bp[h * S];
+              const float2 bs = make_float2(bv.y, bv.x);
+#pragma unroll
+              for (int i = 0; i < RT; ++i) {
+                PQ[i] = __ffma2_rn(a[i][h], bv, PQ[i]);
+                RS[i] = __ffma2_rn(a[i][h], bs, RS[i]);
+              }
+            }
 #pragma unroll
             for (int i = 0; i < RT; ++i) {
-              PQ[i] = __ffma2_rn(a[i][h], bv, PQ[i]);
-              RS[i] = __ffma2_rn(a[i][h], bs, RS[i]);
+              const float re = slot0 ? PQ[i].x : PQ[i].x + PQ[i].y;
+              const float im = slot0 ? PQ[i].y : RS[i].x - RS[i].y;
+              sp[((g * RT + i) * TB + u * TBL + jj) * SP + s] = make_float2(re, im);
             }
           }
-          float P[RT], Qa[RT], Ra[RT], Sa[RT];
-#pragma unroll
-          for (int i = 0; i < RT; ++i) {
-            P[i] = PQ[i].x;
-            Qa[i] = PQ[i].y;
-            Ra[i] = RS[i].x;
-            Sa[i] = RS[i].y;
-          }
-#pragma unroll
-          for (int i = 0; i < RT; ++i) {
-            const float re = slot0 ? P[i] : P[i] + Qa[i];
-            const float im = slot0 ? Qa[i] : Ra[i] - Sa[i];
-            sp[((g * RT + i) * TB + jj) * SP + s] = make_float2(re, im);
-          }
+        }
+        // every contraction thread is done with copy L's buffer: refill it with copy L + 2
+        named_sync(kBarCW, CT);
+        if (tid == 0 && L + 2 < total_loads && *reinterpret_cast<volatile int*>(abort_flag) == 0) {
+          issue(L + 2);
+          issued_upto = L + 2;
         }
       }
       named_arrive(kBarFull0 + (it & 1), CT + FT);
     }
     // copies issued but not waited for (only after a timeout): wait, bounded
-    if (tid == 0 && total > 0 && waited_upto < total - 1) {
-      const int last = total - 1;
-      (void)mbar_wait_bounded(&mbar[last & 1], (last >> 1) & 1, kWaitBudget);
+    if (tid == 0) {
+      for (long long L = waited_upto + 1; L <= issued_upto; ++L)
+        (void)mbar_wait_bounded(&mbar[L & 1], (uint32_t)((L >> 1) & 1), kWaitBudget);
     }
   } else {
     // =========================== FFT warps ===========================
+    if constexpr (C::kRegSplit) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(C::kRegF));
     const int ftid = tid - CT;
     const int ft = ftid % F;
     const float s2 = p.inv_sigma2;
