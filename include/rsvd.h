@@ -172,6 +172,14 @@ int rsvd_build_radial_svd_grouped(int R, int Q, const double* w, const void* tem
  * - Every call uses the same array and it keeps the last call's contents:
  *   calls that overlap on the GPU (other streams, other host threads on the
  *   same device) race; serialise them.
+ * - The looked-up address is kept for the life of the process: a
+ *   cudaDeviceReset (or a different driver context) between calls is not
+ *   supported.
+ * - The fixed array holds fewer per-slice partial sums of C than a caller
+ *   workspace: five template slices at R = 128 (20 CTAs for the sums, 304
+ *   with a workspace), four at R = 129 (36 CTAs), one at R = 181 (9 CTAs);
+ *   for large R or N_B this entry point is therefore slower than
+ *   rsvd_build_radial_svd.
  * Arguments and results are those of rsvd_build_radial_svd without the
  * workspace; results agree with it to rounding (the partial sums over
  * templates are grouped differently). */

@@ -90,3 +90,12 @@ def frob_rel(a, b):
 
 def two_pi():
     return 2 * math.pi
+
+
+def oracle_template_grad_chunk(job):
+    """Oracle gradient of sum_n L_n with respect to the compressed templates
+    `jsel`, summed over one chunk of images (each image's L_n spans every
+    template, so the chunk's contribution is exact). Runs in a spawned worker."""
+    a_c, b_c, inv_sigma2, jsel = job
+    _, _, _, G_bc = O.lse_grad_compressed(a_c, b_c, inv_sigma2)
+    return G_bc[jsel]

@@ -209,3 +209,46 @@ def test_differentiation_workload_sampled_parity():
     assert np.max(np.abs(L[idx].cpu().numpy() - Ln)) < 1e-5 * np.max(np.abs(Ln))
     got = gA.view(N_A, T, H, Q // 2, 2)[idx].cpu().numpy()
     assert _rel(got, pack_slots(G_ac)) < GTOL
+
+
+def test_differentiation_workload_template_gradient_elementwise():
+    """Differentiation workload at full size (4096 images x 256 templates,
+    Q = 256, 3x3 translations, H = 12, sigma^2 = 1): the gradient of 4 sampled
+    templates, every element, against the FP64 oracle summed over all 4096
+    images (chunks of 64 images on spawned host processes)."""
+    import multiprocessing as mp
+    import os
+
+    from synthetic import CONFIGS, make_workload_torch
+    from tests.gpu_common import oracle_template_grad_chunk
+
+    cfg = CONFIGS["gradient"]
+    grid, deltas, tmpl, imgs, _ = make_workload_torch(**cfg, seed=5, device=DEV)
+    H, Q = cfg["H"], cfg["Q"]
+    N_A, N_B = cfg["N_A"], cfg["N_B"]
+    U, _ = P.build_radial_svd(grid.w, tmpl, H)
+    cA = P.compress(grid.k, grid.w, U, imgs, deltas=deltas)
+    cB = P.compress(grid.k, grid.w, U, tmpl)
+    T = deltas.shape[0]
+    _, _, lse = P.align_best(cA, N_A, T, cB, N_B, H, Q, want_lse=True)
+    L = P.lse_rows(lse)
+    gL = torch.ones(N_A, dtype=torch.float32, device=DEV)
+    _, gB = P.lse_backward(cA, N_A, T, cB, N_B, H, Q, 1.0, L, gL)
+    P.status()
+
+    rng = np.random.default_rng(6)
+    jsel = np.sort(rng.choice(N_B, 4, replace=False))
+    Un = U.cpu().numpy()
+    B = tmpl.cpu().numpy().astype(np.complex128)
+    b_c = O.compress(B, Un, grid.w)
+    A_all = imgs.cpu().numpy()
+    jobs = []
+    for n0 in range(0, N_A, 64):
+        A = A_all[n0:n0 + 64].astype(np.complex128)
+        jobs.append((O.compress(O.translate(A, grid.k, deltas), Un, grid.w), b_c, 1.0, jsel))
+    n = min(len(os.sched_getaffinity(0)), 16)
+    with mp.get_context("spawn").Pool(n) as pool:
+        parts = pool.map(oracle_template_grad_chunk, jobs)
+    G_ref = np.sum(parts, axis=0)  # [4, H, Q] full spectrum
+    got = gB.view(N_B, H, Q // 2, 2)[torch.from_numpy(jsel).to(DEV)].cpu().numpy()
+    assert _rel(got, pack_slots(G_ref)) < GTOL

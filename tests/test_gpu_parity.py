@@ -121,6 +121,25 @@ def test_align_best_matches_oracle(Q, R, H, T_side, N_A, N_B):
     P.status()
 
 
+@pytest.mark.parametrize("Q,R,H,T_side,N_A,N_B", [(256, 64, 12, 3, 7, 13), (256, 64, 16, 2, 5, 4),
+                                                   (512, 48, 16, 2, 5, 4), (512, 40, 12, 3, 9, 5)])
+def test_single_role_kernel_selection_matches_oracle(monkeypatch, Q, R, H, T_side, N_A, N_B):
+    """RSVD_ALIGN_KERNEL=fused runs the single-role fused kernel where the
+    warp-specialised one is the default (Q = 256, 512; H <= 16): same oracle
+    bounds, and the same results as the default kernel up to rounding."""
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, seed=Q * 5 + H)
+    cA, cB, T = _gpu(wl, A, B, U)
+    Xr, _, _ = oracle_scores(wl, A, B, U)
+    ref = P.align_best(cA, N_A, T, cB, N_B, H, Q, inv_sigma2=1.0, want_lse=True)
+    monkeypatch.setenv("RSVD_ALIGN_KERNEL", "fused")
+    best, arg, lse = P.align_best(cA, N_A, T, cB, N_B, H, Q, inv_sigma2=1.0, want_lse=True)
+    monkeypatch.delenv("RSVD_ALIGN_KERNEL")
+    check_best(Xr, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
+    scale = torch.clamp(ref[0].abs(), min=1e-30)
+    assert float(((best - ref[0]).abs() / scale).max()) <= 2e-6
+    P.status()
+
+
 @pytest.mark.parametrize("inv_sigma2", [0.25, 4.0])
 def test_lse_scale(inv_sigma2):
     wl, A, B, U = setup(N=128, R=64, Q=256, N_B=6, N_A=4, T_side=3, H=12, seed=9)

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+import oracle as O  # noqa: E402
 import paper_2202_07235_gb300 as P  # noqa: E402
 from synthetic import make_workload  # noqa: E402
 
@@ -41,12 +42,31 @@ def test_noalloc_build_matches_workspace_build_on_two_calls_in_a_row():
         U_na, e_na = P.build_radial_svd_noalloc(wl.grid.w, B, c["H"])
         P.status()
         _compare(U_na, e_na, U_ref, e_ref)
+        # and directly against the FP64 oracle on the same (complex64) templates
+        C = O.radial_kernel(wl.templates.astype(np.complex64).astype(np.complex128), wl.grid.w)
+        U_o, e_o = O.principal_vectors(C, c["H"])
+        _compare(U_na, e_na, torch.from_numpy(U_o), torch.from_numpy(e_o))
 
 
-def test_noalloc_build_rejects_grids_beyond_its_scratch():
+def test_noalloc_build_largest_grid_fits_exactly():
+    """R = 181 is the largest grid whose four R x R FP64 matrices fit the 1 MiB
+    scratch (4 x 262,144 bytes, one template slice)."""
+    wl = make_workload(N=362, R=181, Q=16, N_B=3, N_A=1, snr=None, seed=2)
+    B = torch.from_numpy(wl.templates.astype(np.complex64)).to("cuda:0")
+    U_na, e_na = P.build_radial_svd_noalloc(wl.grid.w, B, 4)
+    P.status()
+    U_ref, e_ref = P.build_radial_svd(wl.grid.w, B, 4)
+    _compare(U_na, e_na, U_ref, e_ref)
+    C = O.radial_kernel(wl.templates.astype(np.complex64).astype(np.complex128), wl.grid.w)
+    U_o, e_o = O.principal_vectors(C, 4)
+    _compare(U_na, e_na, torch.from_numpy(U_o), torch.from_numpy(e_o))
+
+
+@pytest.mark.parametrize("R", [182, 192])
+def test_noalloc_build_rejects_grids_beyond_its_scratch(R):
     from paper_2202_07235_gb300._native import RSVDError
 
-    wl = make_workload(N=384, R=192, Q=32, N_B=2, N_A=1, snr=None, seed=1)
+    wl = make_workload(N=2 * R, R=R, Q=32, N_B=2, N_A=1, snr=None, seed=1)
     B = torch.from_numpy(wl.templates.astype(np.complex64)).to("cuda:0")
     with pytest.raises(RSVDError) as e:
         P.build_radial_svd_noalloc(wl.grid.w, B, 4)
