@@ -220,7 +220,8 @@ def _form_roofline(P, fp, N_A, N_B, T, H, Q, align_ms, sm_count):
     # MMA count: tiles of 128 rows (whole images) x 512/Q templates, 32 slot groups,
     # K = 2 Hp g per group in steps of 16
     g = Q // 64
-    Hp = -(-H // (8 // g)) * (8 // g)
+    step = 2 if g >= 8 else 8 // g
+    Hp = -(-H // step) * step
     tiles = (-(-N_A // (128 // T))) * (-(-N_B // (512 // Q)))
     mma = tiles * 32 * (2 * Hp * g // 16) * terms
     # instruction floor: 39.4 cycles per M=128 N=16 K=16 MMA issued back to back

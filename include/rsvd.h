@@ -62,11 +62,10 @@ enum rsvd_status_code {
  *                lo = rn_bf16(x - hi); the products a_hi b_hi + a_hi b_lo + a_lo b_hi
  *                summed in FP32 on the tensor cores (about 16 significand bits)
  * Step 2 (the transform over q) and the reductions run in FP32 for every form.
- * The three tensor-core forms support Q in {128, 256}, H <= 32, T <= 64
- * (else RSVD_EUNSUPPORTED) in rsvd_compress (shared-memory compression kernel:
- * R * Q <= 24576), rsvd_pack, rsvd_align_scores and rsvd_align_best; scoring
- * with RSVD_BF16X3 at Q = 256 takes H <= 18 (shared memory). The gradient
- * entry points take RSVD_FP32 only. */
+ * The three tensor-core forms support Q in {128, 256, 512}, H <= 32, T <= 64
+ * (else RSVD_EUNSUPPORTED) in rsvd_compress, rsvd_pack, rsvd_align_scores and
+ * rsvd_align_best; scoring with RSVD_BF16X3 at Q = 256 and 512 takes H <= 18
+ * (shared memory). The gradient entry points take RSVD_FP32 only. */
 enum rsvd_precision { RSVD_FP32 = 0, RSVD_BF16 = 1, RSVD_FP16 = 2, RSVD_BF16X3 = 3 };
 
 /* RSVD_ABI_VERSION of the loaded library. */
@@ -212,7 +211,8 @@ int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, const void* tem
  * Layout of `out` for RSVD_BF16 / RSVD_FP16 / RSVD_BF16X3 (the tensor-core
  * operand form): one plane of 16-bit floats (BF16X3: a hi plane, then a lo
  * plane of the same size). With g = Q/64 slots per group, Hp = H rounded up so
- * that K = 2*Hp*g is a multiple of 16, IPT = 128/T objects per tile and
+ * that K = 2*Hp*g is a multiple of 16 (and Hp even at Q = 512), IPT = 128/T
+ * objects per tile and
  * tiles = ceil(N/IPT), a plane is the array
  *   [tiles][32 groups][K/8][128 lanes][8]
  * where component (re: c = 0, im: c = 1) of (object n, translation t, vector h,

@@ -52,6 +52,7 @@ constexpr int kTcThreads = 352;  // warps 0, 10 producers; 1 MMA; 2..9 epilogue
 constexpr int kEpiThreads = 256;
 constexpr long long kTcBudget = 1LL << 31;  // clock cycles per bounded wait
 constexpr int kBarEpi = 1;
+constexpr int kBarEpiStage = 2;  // between the two Step-2 stages of shared pairs (Q = 512)
 constexpr int kTmemCols = 512;
 
 template <int Q>
@@ -59,7 +60,11 @@ struct TcCfg {
   static constexpr int M = Q / 2;      // points of the half-length DFT (= packed slots)
   static constexpr int g = Q / 64;     // slots per group
   static constexpr int NT = 512 / Q;   // templates per tile
-  static constexpr int TPT = NT / 2;   // templates per epilogue thread
+  // templates per epilogue thread; at Q = 512 (one template per tile) the two
+  // warps of a lane quadrant share each pair instead (kShare)
+  static constexpr bool kShare = NT == 1;
+  static constexpr int TPT = kShare ? 1 : NT / 2;
+  static constexpr int RES = kShare ? 2 : NT;  // result slots per row and tile
 };
 
 struct TcParams {
@@ -73,12 +78,14 @@ struct TcParams {
   int* status;
   int N_A, T, N_B, IPT, nRT, nTP, CH, nUnits;
   int K, KC, KS, Hp, stages, split, lse_on, nprod;
+  int nspl;  // stages per group: the group's K-steps in nspl equal parts (KS K-steps each)
   int bres;  // template blocks of all 32 groups resident for a whole work unit (single-pass forms)
   float inv_sigma2;
   uint32_t idesc;
+  // a_bytes, b_bytes: one stage's A and B blocks per plane (a group's part of K)
   uint32_t stage_bytes, a_bytes, b_bytes, dense_off, dense_bytes, bres_off, res_off, bar_off;
-  float2 WQ[128];  // W_Q^k = exp(-2 pi i k / Q), k < Q/2
-  float2 WM[128];  // W_M^k, M = Q/2
+  float2 WQ[256];  // W_Q^k = exp(-2 pi i k / Q), k < Q/2
+  float2 WM[256];  // W_M^k, M = Q/2
 };
 
 // Bounded wait for a barrier phase. The abort flag and the clock are checked
@@ -104,12 +111,14 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
 
 // The MMA chain of one group: K-steps ks = 0..KS-1 (descriptor start addresses
 // advance by a_step / b_step), bf16x3 adding the A_hi B_lo and A_lo B_hi terms.
+// `acc0` = 1 when the chain continues a group's accumulation from an earlier stage.
 template <int KS, bool kSplit>
 __device__ __forceinline__ void issue_group(uint32_t leader, uint32_t d, uint64_t ad, uint64_t bd, uint64_t ad_lo,
-                                            uint64_t bd_lo, uint64_t a_step, uint64_t b_step, uint32_t idesc) {
+                                            uint64_t bd_lo, uint64_t a_step, uint64_t b_step, uint32_t idesc,
+                                            uint32_t acc0) {
 #pragma unroll
   for (int ks = 0; ks < KS; ++ks) {
-    tc_mma_f16_by(leader, d, ad + ks * a_step, bd + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+    tc_mma_f16_by(leader, d, ad + ks * a_step, bd + ks * b_step, idesc, (ks > 0 || acc0) ? 1u : 0u);
     if (kSplit) {
       tc_mma_f16_by(leader, d, ad + ks * a_step, bd_lo + ks * b_step, idesc, 1u);
       tc_mma_f16_by(leader, d, ad_lo + ks * a_step, bd + ks * b_step, idesc, 1u);
@@ -151,16 +160,16 @@ __device__ __forceinline__ void issue_two_groups_rt(int KS, uint32_t leader, uin
 template <bool kSplit>
 __device__ __forceinline__ void issue_group_rt(int KS, uint32_t leader, uint32_t d, uint64_t ad, uint64_t bd,
                                                uint64_t ad_lo, uint64_t bd_lo, uint64_t a_step, uint64_t b_step,
-                                               uint32_t idesc) {
+                                               uint32_t idesc, uint32_t acc0) {
   switch (KS) {
-    case 2: issue_group<2, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
-    case 3: issue_group<3, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
-    case 4: issue_group<4, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
-    case 6: issue_group<6, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
-    case 8: issue_group<8, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc); return;
+    case 2: issue_group<2, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc, acc0); return;
+    case 3: issue_group<3, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc, acc0); return;
+    case 4: issue_group<4, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc, acc0); return;
+    case 6: issue_group<6, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc, acc0); return;
+    case 8: issue_group<8, kSplit>(leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, idesc, acc0); return;
     default:
       for (int ks = 0; ks < KS; ++ks) {
-        tc_mma_f16_by(leader, d, ad + ks * a_step, bd + ks * b_step, idesc, ks > 0 ? 1u : 0u);
+        tc_mma_f16_by(leader, d, ad + ks * a_step, bd + ks * b_step, idesc, (ks > 0 || acc0) ? 1u : 0u);
         if (kSplit) {
           tc_mma_f16_by(leader, d, ad + ks * a_step, bd_lo + ks * b_step, idesc, 1u);
           tc_mma_f16_by(leader, d, ad_lo + ks * a_step, bd + ks * b_step, idesc, 1u);
@@ -177,24 +186,19 @@ __device__ __forceinline__ float2 zform(float2 X, float2 P, float2 w) {
   return make_float2(A.x - C.y, A.y + C.x);
 }
 
-// Step 2 and the per-row reduction for one (image row, template jj) pair.
-// Returns (max of X / 2pi over m, its m, lse max, lse sum) with the lse in units
-// of inv_sigma2 * X; writes X instead when kWriteX.
-template <int Q, bool kWriteX>
-__device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj, bool row_ok, float* xrow) {
-  using C = TcCfg<Q>;
-  constexpr int g = C::g;
-  const uint32_t cb = (uint32_t)(jj * 2 * g);
-
-  // ---- first stage: pre-processing, g-point DFTs, twiddles; in place ----
-  // (the loads of the next group pair are in flight while this one is computed)
+// Step 2, first stage, for group pairs k1 = K1B .. K1E-1 of one (image row,
+// template jj) pair: pre-processing, g-point DFTs, twiddles; in place. The
+// loads of the next group pair are in flight while this one is computed.
+template <int Q, int K1B, int K1E>
+__device__ __forceinline__ void tc_first_stage(const TcParams& p, uint32_t tl, uint32_t cb) {
+  constexpr int g = TcCfg<Q>::g;
   uint32_t cur[4 * g], nxt[4 * g];
-  tmem_ld_pair_issue<g>(tl + cb, tl + cb, cur);
+  tmem_ld_pair_issue<g>(tl + K1B * 16 + cb, tl + ((32 - K1B) & 31) * 16 + cb, cur);
   tmem_wait_ld_tie<4 * g>(cur);
 #pragma unroll
-  for (int k1 = 0; k1 <= 16; ++k1) {
+  for (int k1 = K1B; k1 < K1E; ++k1) {
     const int k2 = (32 - k1) & 31;
-    if (k1 < 16) tmem_ld_pair_issue<g>(tl + (k1 + 1) * 16 + cb, tl + ((31 - k1) & 31) * 16 + cb, nxt);
+    if (k1 + 1 < K1E) tmem_ld_pair_issue<g>(tl + (k1 + 1) * 16 + cb, tl + ((31 - k1) & 31) * 16 + cb, nxt);
     float2 xa[g], xb[g], za[g], zb[g];
 #pragma unroll
     for (int i = 0; i < g; ++i) {
@@ -229,21 +233,28 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
       for (int p1 = 1; p1 < g; ++p1) zb[p1] = cmul(zb[p1], p.WM[k2 * p1]);
       tmem_st<g>(tl + k2 * 16 + cb, zb);
     }
-    if (k1 < 16) {
+    if (k1 + 1 < K1E) {
       tmem_wait_ld_tie<4 * g>(nxt);
 #pragma unroll
       for (int i = 0; i < 4 * g; ++i) cur[i] = nxt[i];
     }
   }
-  tmem_wait_st();
+}
 
-  // ---- second stage: 32-point DFTs over k1, reductions ----
+// Step 2, second stage, for p1 = P1B .. P1E-1: 32-point DFTs over k1 (column
+// 2 p1 of every group) and the reductions. Returns (max of X / 2pi over those
+// m, its m, lse max, lse sum) with the lse in units of inv_sigma2 * X; writes
+// X instead when kWriteX.
+template <int Q, bool kWriteX, int P1B, int P1E>
+__device__ __forceinline__ float4 tc_second_stage(const TcParams& p, uint32_t tl, uint32_t cb, bool row_ok,
+                                                  float* xrow) {
+  constexpr int g = TcCfg<Q>::g;
   constexpr float kTwoPi = 6.283185307179586f;
   const float cs = kTwoPi * p.inv_sigma2;
   float best = -INFINITY, lm = -INFINITY, ls = 0.0f;
   int bm = 0;
 #pragma unroll
-  for (int p1 = 0; p1 < g; ++p1) {
+  for (int p1 = P1B; p1 < P1E; ++p1) {
     float2 z[32];
     {
       uint32_t r[4][16];  // all 32 loads of the pass in flight, then one wait
@@ -290,6 +301,39 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
   return make_float4(best, __int_as_float(bm), lm, ls);
 }
 
+// Step 2 and the per-row reduction for one (image row, template jj) pair by
+// one thread (Q <= 256): the real Q-point transform of the half spectrum as a
+// complex M = Q/2 point DFT of
+//   Z(k) = [X_hat(k) + conj X_hat(M - k)] + i W_Q^k [X_hat(k) - conj X_hat(M - k)],
+// split as M = g x 32 (see the file header).
+template <int Q, bool kWriteX>
+__device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj, bool row_ok, float* xrow) {
+  constexpr int g = TcCfg<Q>::g;
+  const uint32_t cb = (uint32_t)(jj * 2 * g);
+  tc_first_stage<Q, 0, 17>(p, tl, cb);
+  tmem_wait_st();
+  return tc_second_stage<Q, kWriteX, 0, g>(p, tl, cb, row_ok, xrow);
+}
+
+// The same at Q = 512 (one template per tile) shared by the two warps of a
+// lane quadrant: warp `sub` takes group pairs k1 = 0..8 (sub 0) or 9..16
+// (sub 1) of the first stage and p1 = 0..3 or 4..7 of the second; between the
+// stages every epilogue thread meets at a named barrier. Returns the partial
+// reduction over this warp's angles.
+template <int Q, bool kWriteX>
+__device__ __forceinline__ float4 tc_pair_shared(const TcParams& p, uint32_t tl, int sub, bool row_ok, float* xrow) {
+  constexpr int g = TcCfg<Q>::g;
+  static_assert(g == 8, "shared pairs are laid out for g = 8");
+  if (sub == 0) tc_first_stage<Q, 0, 9>(p, tl, 0);
+  else tc_first_stage<Q, 9, 17>(p, tl, 0);
+  tmem_wait_st();
+  tc_fence_before();
+  named_sync(kBarEpiStage, kEpiThreads);
+  tc_fence_after();
+  if (sub == 0) return tc_second_stage<Q, kWriteX, 0, g / 2>(p, tl, 0, row_ok, xrow);
+  return tc_second_stage<Q, kWriteX, g / 2, g>(p, tl, 0, row_ok, xrow);
+}
+
 // kPair: single-pass forms with resident template blocks (the producers only
 // issue copies) take two groups from two consecutive stages per MMA step, their
 // chains interleaved; the other plans keep one group per step.
@@ -307,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
   volatile uint32_t* abort_flag = tmem_slot + 1;
   // template rows [plane][jj][group][K], one copy per producer warp
   uint16_t* dense = reinterpret_cast<uint16_t*>(tc_smem + p.dense_off + (threadIdx.x >= 320 ? p.dense_bytes : 0u));
-  float4* res = reinterpret_cast<float4*>(tc_smem + p.res_off);          // [2][NT][128]
+  float4* res = reinterpret_cast<float4*>(tc_smem + p.res_off);          // [2][RES][128]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int planes = p.split ? 2 : 1;
@@ -350,9 +394,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
     // every group: source word in the template rows (group 0, plane 0),
     // destination word in the block, slot-0 flag (u == 0).
     constexpr int kMaxItems = 8;  // NT * g * Hp / 32 with Hp <= 32
+    // With p.nspl = 2 an item lies in one half of the group's K range (it_kh),
+    // and its destination is relative to that half's block.
     int it_src[kMaxItems], it_dst[kMaxItems];
-    uint32_t it_u0 = 0u;
+    uint32_t it_u0 = 0u, it_kh = 0u;
     const int n_items = NT * g * p.Hp;
+    const int k_part = p.K / p.nspl;
 #pragma unroll
     for (int r = 0; r < kMaxItems; ++r) {
       const int i = lane + 32 * r;
@@ -363,10 +410,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
         const int q = i / p.Hp;
         const int u = q % g, jj = q / g;
         const int k = u * 2 * p.Hp + 2 * h;
+        const int kh = k / k_part, kl = k - kh * k_part;
         const int nr = jj * 2 * g + 2 * u;
         it_src[r] = (jj * kOpGroups * p.K + k) >> 1;
-        it_dst[r] = ((((k >> 3) * 16 + nr) * 8) + (k & 7)) >> 1;
+        it_dst[r] = ((((kl >> 3) * 16 + nr) * 8) + (kl & 7)) >> 1;
         if (u == 0) it_u0 |= 1u << r;
+        if (kh) it_kh |= 1u << r;
       }
     }
     const uint32_t* dense_w = reinterpret_cast<const uint32_t*>(dense);
@@ -436,7 +485,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
         __syncwarp();
       }
       for (int rt = rt0; rt < rt1 && ok; ++rt, ++ptile) {
-        for (int grp = 0; grp < kOpGroups; ++grp) {
+        for (int gi = 0; gi < kOpGroups * p.nspl; ++gi) {
+          const int grp = gi / p.nspl, kh = gi - grp * p.nspl;  // group, part of its K range
           const int s = ps;
           if (p.nprod == 2 && (it & 1) != mine) {
             ++it;
@@ -458,7 +508,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           unsigned char* st = tc_smem + (size_t)s * p.stage_bytes;
           if (lane == 0) {
             mbar_arrive_expect_tx(&full[s], planes * p.a_bytes);
-            const long long off = ((long long)rt * kOpGroups + grp) * p.KC * kOpLanes * 8;
+            const long long off = (((long long)rt * kOpGroups + grp) * p.KC + (long long)kh * (p.KC / p.nspl)) *
+                                  kOpLanes * 8;
             for (int pl = 0; pl < planes; ++pl) bulk_g2s(st + pl * p.a_bytes, p.a + pl * p.a_plane + off, p.a_bytes, &full[s]);
           }
           // block-diagonal template operand: rows (jj, u, re/im), K-major core matrices
@@ -466,7 +517,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           const int gofs = grp * p.K / 2;
 #pragma unroll
           for (int r = 0; r < (p.bres ? 0 : kMaxItems); ++r) {
-            if (it_src[r] < 0) continue;
+            if (it_src[r] < 0 || (int)((it_kh >> r) & 1u) != kh) continue;
             const bool slot0 = grp == 0 && ((it_u0 >> r) & 1u);
             for (int pl = 0; pl < planes; ++pl) {
               const uint32_t v = dense_w[pl * dense_plane_w + gofs + it_src[r]];
@@ -548,7 +599,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
             ms = (s1 + 1 == p.stages) ? 0 : s1 + 1;
             mphase = (s1 + 1 == p.stages) ? (ph1 ^ 1u) : ph1;
           }
-          for (int grp = 0; !kPair && grp < kOpGroups; ++grp) {
+          for (int gi = 0; !kPair && gi < kOpGroups * p.nspl; ++gi) {
+            const int grp = gi / p.nspl, kh = gi - grp * p.nspl;
             const int s = ms;
             if (!__all_sync(0xffffffffu, tc_wait(&full[s], mphase, abort_flag, p.status))) {
               ok = false;
@@ -566,11 +618,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
             const uint64_t ad = smem_desc_kmajor(a_hi, a_lbo, kSbo), bd = smem_desc_kmajor(b_hi, b_lbo, kSbo);
             const uint64_t a_step = (2u * a_lbo) >> 4, b_step = (2u * b_lbo) >> 4;
             const uint32_t leader = mma_leader;
+            const uint32_t acc0 = kh > 0 ? 1u : 0u;  // later parts continue the group's accumulation
             if (!p.split) {
-              issue_group_rt<false>(p.KS, leader, d, ad, bd, 0, 0, a_step, b_step, p.idesc);
+              issue_group_rt<false>(p.KS, leader, d, ad, bd, 0, 0, a_step, b_step, p.idesc, acc0);
             } else {
               const uint64_t ad_lo = smem_desc_kmajor(a_lo, a_lbo, kSbo), bd_lo = smem_desc_kmajor(b_lo, b_lbo, kSbo);
-              issue_group_rt<true>(p.KS, leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, p.idesc);
+              issue_group_rt<true>(p.KS, leader, d, ad, bd, ad_lo, bd_lo, a_step, b_step, p.idesc, acc0);
             }
             tc_commit_by(leader, &empty[s]);
             __syncwarp();
@@ -610,18 +663,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
         float4 r[TPT];
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
-          const int jj = sub * TPT + i;
+          const int jj = C::kShare ? 0 : sub * TPT + i;
           const int j = tp * NT + jj;
           float* xrow = nullptr;
           if (kWriteX) xrow = p.X + ((n * p.T + t) * (long long)p.N_B + j) * (Q);
-          r[i] = tc_pair<Q, kWriteX>(p, tl, jj, row_ok && j < p.N_B, xrow);
+          if constexpr (C::kShare) {
+            r[i] = tc_pair_shared<Q, kWriteX>(p, tl, sub, row_ok && j < p.N_B, xrow);
+          } else {
+            r[i] = tc_pair<Q, kWriteX>(p, tl, jj, row_ok && j < p.N_B, xrow);
+          }
         }
         tc_fence_before();
         mbar_arrive(tmem_empty);
         if (!kWriteX) {
-          float4* rb = res + (size_t)(tile & 1) * NT * kOpLanes;
+          float4* rb = res + (size_t)(tile & 1) * C::RES * kOpLanes;
 #pragma unroll
-          for (int i = 0; i < TPT; ++i) rb[(sub * TPT + i) * kOpLanes + row] = r[i];
+          for (int i = 0; i < TPT; ++i) rb[(sub * TPT + i) * kOpLanes + row] = r[i];  // kShare: slot = sub
         }
         // one decision for all epilogue threads (the flag may change meanwhile)
         if (named_sync_or(kBarEpi, kEpiThreads, *abort_flag != 0u)) {
@@ -633,11 +690,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           const long long nn = (long long)rt * p.IPT + nl;
           const int j = tp * NT + jj;
           if (nn < p.N_A && j < p.N_B) {
-            const float4* rb = res + (size_t)(tile & 1) * NT * kOpLanes + jj * kOpLanes + nl * p.T;
+            const float4* rb = res + (size_t)(tile & 1) * C::RES * kOpLanes + jj * kOpLanes + nl * p.T;
             float bv = -INFINITY, m = -INFINITY, s = 0.0f;
             int ba = 0;
             for (int tt = 0; tt < p.T; ++tt) {
-              const float4 e = rb[tt];
+              float4 e = rb[tt];
+              if constexpr (C::kShare) {  // the two halves of the pair's angles (interleaved m)
+                const float4 e1 = rb[kOpLanes + tt];
+                if (e1.x > e.x || (e1.x == e.x && __float_as_int(e1.y) < __float_as_int(e.y))) {
+                  e.x = e1.x;
+                  e.y = e1.y;
+                }
+                if (p.lse_on) lse_merge(e.z, e.w, e1.z, e1.w);
+              }
               if (e.x > bv) {
                 bv = e.x;
                 ba = tt * Q + __float_as_int(e.y);
@@ -667,17 +732,20 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   p.split = precision == RSVD_BF16X3 ? 1 : 0;
   p.K = La.K;
   p.KC = La.KC;
-  p.KS = La.K / 16;
+  // Q = 512: a group's operand (K = 16 Hp components, 64 KB per plane at H = 16)
+  // arrives in two stages of half its K range (Hp is even there)
+  p.nspl = (Q == 512) ? 2 : 1;
+  p.KS = La.K / 16 / p.nspl;
   p.Hp = La.Hp;
   p.IPT = La.IPT;
   p.nRT = (int)La.tiles;
   p.nTP = (p.N_B + C::NT - 1) / C::NT;
   p.idesc = idesc_f16(precision == RSVD_FP16 ? 0u : 1u, 128, 16);
-  p.a_bytes = (uint32_t)(kOpLanes * La.K * 2);
-  p.b_bytes = (uint32_t)(16 * La.K * 2);
+  p.a_bytes = (uint32_t)(kOpLanes * La.K * 2 / p.nspl);
+  p.b_bytes = (uint32_t)(16 * La.K * 2 / p.nspl);
   const uint32_t dense_bytes = (uint32_t)(planes * C::NT * kOpGroups * La.K * 2);  // per producer warp
   p.dense_bytes = dense_bytes;
-  const uint32_t res_bytes = 2u * C::NT * kOpLanes * 16u;
+  const uint32_t res_bytes = 2u * C::RES * kOpLanes * 16u;
   const uint32_t kMaxSmem = 227u * 1024u;
   // Preferred layouts, first that fits: template blocks resident per unit
   // (single-pass forms) with two producers, then one producer; else the blocks
@@ -687,7 +755,7 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   const Opt opts[] = {{1, 2, 3}, {1, 1, 3}, {0, 2, 3}, {0, 1, 2}};
   bool found = false;
   for (const Opt& o : opts) {
-    if (o.bres && planes != 1) continue;
+    if (o.bres && (planes != 1 || p.nspl != 1)) continue;
     const uint32_t sb = (uint32_t)((planes * (p.a_bytes + (o.bres ? 0u : p.b_bytes)) + 1023) / 1024 * 1024);
     const uint32_t fx = (uint32_t)o.nprod * dense_bytes + (o.bres ? bres_bytes : 0u) + res_bytes + 1024u;
     if (fx < kMaxSmem && (int)((kMaxSmem - fx) / sb) >= o.min_stages) {
@@ -703,7 +771,10 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   int stages = (int)((kMaxSmem - fixed) / p.stage_bytes);
   if (stages > 6) stages = 6;
   uint32_t smem = 0;
-  for (; stages >= 2; --stages) {
+  // with two parts per group the stage count is even, so every stage always
+  // holds the same part and its template block keeps one zero pattern
+  for (; stages >= 2; stages -= (p.nspl == 2 && (stages & 1) == 0) ? 2 : 1) {
+    if (p.nspl == 2 && (stages & 1)) continue;
     p.stages = stages;
     p.dense_off = (uint32_t)stages * p.stage_bytes;
     p.bres_off = p.dense_off + (uint32_t)p.nprod * dense_bytes;
@@ -772,7 +843,8 @@ RSVD_HIDDEN int align_tc(const void* cA, int N_A, int T, const void* cB, int N_B
   p.lse_on = lse ? 1 : 0;
   p.inv_sigma2 = inv_sigma2;
   if (Q == 128) return launch_tc<128>(p, X != nullptr, La, precision, stream);
-  return launch_tc<256>(p, X != nullptr, La, precision, stream);
+  if (Q == 256) return launch_tc<256>(p, X != nullptr, La, precision, stream);
+  return launch_tc<512>(p, X != nullptr, La, precision, stream);
 }
 
 }  // namespace rsvd

@@ -26,10 +26,12 @@ constexpr int kHB = 16;  // principal vectors per register block
 
 struct CompressParams {
   const float2* polar;  // [N][R][Q]
-  float2* out;          // [N*T][H][Q/2]
+  float2* out;          // [N*T][H][Q/2] (RSVD_FP32)
+  uint16_t* planes;     // operand planes (other precisions; layout L)
+  OperandLayout L;
   const double* U;      // [R][H]
   int* status;
-  int N, R, Q, H, T, Hpad, log2Q;
+  int N, R, Q, H, T, Hpad, log2Q, precision;
   float k[kMaxR];
   float sw[kMaxR];
   float dx[kMaxT];
@@ -130,8 +132,12 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(const __grid_constan
           float2 v = (s == 0) ? make_float2(x[0].x, x[M].x) : x[s];
           v.x *= invQ;
           v.y *= invQ;
-          const size_t row = (size_t)n * T + tt;
-          p.out[(row * H + h) * M + s] = v;
+          if (p.precision == RSVD_FP32) {
+            const size_t row = (size_t)n * T + tt;
+            p.out[(row * H + h) * M + s] = v;
+          } else {
+            operand_put(p.planes, p.L.plane_elems, p.precision, operand_index(p.L, n, tt, h, s), v);
+          }
         }
       }
       __syncthreads();
@@ -158,8 +164,7 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
   OperandLayout OL{};
   const bool fits_v2 = R * (Q / 2) * 8 <= 96 * 1024;
   if (precision != RSVD_FP32) {
-    // operand forms are written by the shared-memory kernel only
-    if (!is_operand_precision(precision) || !fits_v2) return RSVD_EUNSUPPORTED;
+    if (!is_operand_precision(precision)) return RSVD_EUNSUPPORTED;
     if (!make_operand_layout(N, T, H, Q, &OL)) return RSVD_EUNSUPPORTED;
   }
   if (((uintptr_t)polar & 7u) || ((uintptr_t)out & 15u) || ((uintptr_t)U & 7u)) return RSVD_EINVAL;
@@ -175,6 +180,9 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
   p.Q = Q;
   p.H = H;
   p.T = T;
+  p.precision = precision;
+  p.planes = static_cast<uint16_t*>(out);
+  p.L = OL;
   p.Hpad = (H + kHB - 1) / kHB * kHB;
   int lg = 0;
   while ((1 << lg) < Q) ++lg;
@@ -187,6 +195,11 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
   for (int t = 0; t < T; ++t) {
     p.dx[t] = deltas ? (float)deltas[2 * t] : 0.0f;
     p.dy[t] = deltas ? (float)deltas[2 * t + 1] : 0.0f;
+  }
+  if (precision != RSVD_FP32) {
+    // padding components, lanes and tiles of the operand planes are zero
+    const size_t bytes = (size_t)operand_planes(precision) * (size_t)OL.plane_elems * 2;
+    if (cudaMemsetAsync(out, 0, bytes, static_cast<cudaStream_t>(stream)) != cudaSuccess) return RSVD_ECUDA;
   }
   {
     // shared-memory kernel when half of one object's rings fits (compress_v2.cu)
@@ -205,11 +218,7 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
     q.precision = precision;
     q.planes = static_cast<uint16_t*>(out);
     q.L = OL;
-    if (precision != RSVD_FP32) {
-      // padding components, lanes and tiles of the operand planes are zero
-      const size_t bytes = (size_t)operand_planes(precision) * (size_t)OL.plane_elems * 2;
-      if (cudaMemsetAsync(out, 0, bytes, static_cast<cudaStream_t>(stream)) != cudaSuccess) return RSVD_ECUDA;
-    }
+
     q.dk = (float)k[0];
     for (int r = 0; r < R; ++r) {
       q.k[r] = p.k[r];
@@ -220,7 +229,7 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
       q.dy[t] = p.dy[t];
     }
     const int rc2 = fits_v2 ? launch_compress_v2(q, static_cast<cudaStream_t>(stream)) : RSVD_EUNSUPPORTED;
-    if (rc2 != RSVD_EUNSUPPORTED || precision != RSVD_FP32) return rc2;
+    if (rc2 != RSVD_EUNSUPPORTED) return rc2;
   }
   const int M = Q / 2;
   const int L = M < kThreads ? M : kThreads;

@@ -9,11 +9,11 @@
 //   RSVD_BF16X3 hi = rn_bf16(x), lo = rn_bf16(x - hi)  (2 planes: hi, then lo)
 // with x the FP32 coefficient.
 //
-// Geometry (G = 32 column groups, g = Q/64 slots per group, nG * g = Q/2):
+// Geometry (G = 32 column groups, g = Q/64 slots per group, G * g = Q/2):
 //   slot s belongs to group s % 32 at position u = s / 32;
 //   K = 2 * Hp * g components per (object row, group), k = u * 2 Hp + 2 h + c
 //   (c = 0: re, 1: im), Hp = H rounded up so that K is a multiple of 16
-//   (components of h >= H are zero);
+//   (and to an even number at Q = 512; components of h >= H are zero);
 //   128 rows per tile: IPT = 128 / T objects per tile, row (lane) = (n % IPT) * T + t;
 //   a plane is [tile][group][k / 8][lane 0..127][k % 8]: each (tile, group)
 //   block is the canonical no-swizzle K-major tensor-core operand image of a
@@ -48,14 +48,16 @@ inline bool is_operand_precision(int precision) {
 inline int operand_planes(int precision) { return precision == RSVD_BF16X3 ? 2 : 1; }
 
 // Layout of N objects x T translations; false if (Q, T, H) is outside the
-// tensor-core path (Q in {128, 256}, T <= 64, H <= 32).
+// tensor-core path (Q in {128, 256, 512}, T <= 64, H <= 32).
 inline bool make_operand_layout(long long N, int T, int H, int Q, OperandLayout* L) {
-  if (!(Q == 128 || Q == 256) || T < 1 || T > kMaxT || H < 1 || H > 32 || N < 1) return false;
+  if (!(Q == 128 || Q == 256 || Q == 512) || T < 1 || T > kMaxT || H < 1 || H > 32 || N < 1) return false;
   L->Q = Q;
   L->T = T;
   L->H = H;
   L->g = Q / 64;
-  const int step = 8 / L->g;  // K = 2 Hp g multiple of 16  <=>  Hp multiple of 8 / g
+  // K = 2 Hp g multiple of 16  <=>  Hp multiple of 8 / g; at Q = 512 Hp is
+  // even, so that a group's K-steps split into two equal halves
+  const int step = L->g >= 8 ? 2 : 8 / L->g;
   L->Hp = (H + step - 1) / step * step;
   L->K = 2 * L->Hp * L->g;
   L->KC = L->K / 8;

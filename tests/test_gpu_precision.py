@@ -32,7 +32,7 @@ FORMS = ("bf16", "fp16", "bf16x3")
 
 def _layout(N, T, H, Q):
     g = Q // 64
-    step = 8 // g
+    step = 2 if g >= 8 else 8 // g  # K = 2 Hp g a multiple of 16; Hp even at Q = 512
     Hp = -(-H // step) * step
     K = 2 * Hp * g
     IPT = 128 // T
@@ -78,11 +78,13 @@ CASES = [  # Q, R, H, T_side, N_A, N_B
     (128, 32, 6, 1, 130, 9),     # H padded to 8; two image tiles; 3 template groups (ragged)
     (256, 64, 12, 3, 30, 5),     # 14 images per tile, ragged last tile and template pair
     (256, 64, 5, 2, 33, 4),      # H padded to 6
+    (512, 48, 16, 3, 29, 3),     # Q = 512: one template per tile, 14 images per tile, ragged
+    (512, 40, 7, 2, 70, 2),      # Q = 512, H padded to 8, three image tiles
 ]
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("Q,R,H,T_side,N_A,N_B", CASES[:2] + CASES[2:3])
+@pytest.mark.parametrize("Q,R,H,T_side,N_A,N_B", CASES[:3] + CASES[4:5])
 def test_pack_is_bit_exact(form, Q, R, H, T_side, N_A, N_B):
     wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=N_B, N_A=N_A, T_side=T_side, H=H, seed=Q + H)
     T = wl.deltas.shape[0]
@@ -95,13 +97,16 @@ def test_pack_is_bit_exact(form, Q, R, H, T_side, N_A, N_B):
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_compress_operand_form_equals_pack_of_fp32(form):
-    wl, A, B, U = setup(N=128, R=64, Q=256, N_B=3, N_A=17, T_side=3, H=12, seed=5)
+@pytest.mark.parametrize("Q,R,H", [(256, 64, 12), (512, 128, 16)])
+def test_compress_operand_form_equals_pack_of_fp32(form, Q, R, H):
+    """Q = 512 with 128 rings goes through the generic compression kernel (the
+    shared-memory kernel holds R Q / 2 <= 12,288 samples)."""
+    wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=3, N_A=17, T_side=3, H=H, seed=5)
     g = wl.grid
     At, Ut = torch.from_numpy(A).to(DEV), torch.from_numpy(U).to(DEV)
     c32 = P.compress(g.k, g.w, Ut, At, deltas=wl.deltas)
     c16 = P.compress(g.k, g.w, Ut, At, deltas=wl.deltas, precision=form)
-    ref = P.pack(c32, 17, 9, 12, 256, form)
+    ref = P.pack(c32, 17, 9, H, Q, form)
     P.status()
     assert torch.equal(c16, ref)
 
@@ -178,15 +183,28 @@ def test_split_bf16x3_throughput_geometry_within_1e5():
     check_best(Xr, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
 
 
-def test_split_bf16x3_noiseless_argmax_identical():
-    """Full rank (H = R = 32) on noiseless images made as T_{-delta_t0} R_{gamma_m0} B_j0."""
+def test_split_bf16x3_large_geometry_within_1e5():
+    """The large workload's geometry (256 px, 128 rings, Q = 512, 5x5
+    translations, H = 16) on 6 images x 3 templates, end to end."""
+    wl, cA, cB, T, Xr = _end_to_end("bf16x3", 512, 128, 16, 5, 6, 3, snr=0.05, seed=13)
+    best, arg, lse = P.align_best(cA, 6, T, cB, 3, 16, 512, want_lse=True, precision="bf16x3")
+    X = P.align_scores(cA, 6, T, cB, 3, 16, 512, precision="bf16x3").cpu().numpy().astype(np.float64)
+    P.status()
+    assert np.linalg.norm(X - Xr) / np.linalg.norm(Xr) <= 1e-5
+    assert _pair_scale_err(X, Xr) <= 1e-5
+    check_best(Xr, best.cpu().numpy(), arg.cpu().numpy(), lse.cpu().numpy(), 1.0)
+
+
+@pytest.mark.parametrize("Q,R", [(128, 32), (512, 16)])
+def test_split_bf16x3_noiseless_argmax_identical(Q, R):
+    """Full rank (H = R) on noiseless images made as T_{-delta_t0} R_{gamma_m0} B_j0
+    (at Q = 512 split operands take H <= 18, hence 16 rings)."""
     from synthetic import make_workload
 
-    Q = 128
-    wl = make_workload(N=64, R=32, Q=Q, N_B=6, N_A=10, snr=None, T_side=3, seed=11)
+    wl = make_workload(N=2 * R, R=R, Q=Q, N_B=6, N_A=10, snr=None, T_side=3, seed=11)
     A = wl.images.astype(np.complex64)
     B = wl.templates.astype(np.complex64)
-    H = 32
+    H = R
     U, _ = O.principal_vectors(O.radial_kernel(B.astype(np.complex128), wl.grid.w), H)
     g = wl.grid
     Ut = torch.from_numpy(U).to(DEV)
@@ -221,15 +239,16 @@ def test_operand_forms_reject_unsupported_sizes():
     def buf(H, Q, form):  # operand buffers large enough for the binding's size check
         return torch.zeros(max(P.compressed_bytes(1, 1, H, Q, form), 64), dtype=torch.uint8, device=DEV)
 
-    x = buf(8, 512, "bf16")
+    x = buf(8, 1024, "bf16")
     with pytest.raises(P.RSVDError):
-        P.align_best(x, 1, 1, x, 1, 8, 512, precision="bf16")
+        P.align_best(x, 1, 1, x, 1, 8, 1024, precision="bf16")
     x = buf(33, 256, "bf16x3")
     with pytest.raises(P.RSVDError):
         P.align_best(x, 1, 1, x, 1, 33, 256, precision="bf16x3")
-    x = buf(20, 256, "bf16x3")
-    with pytest.raises(P.RSVDError):  # split operands at Q = 256: shared memory holds H <= 18
-        P.align_best(x, 1, 1, x, 1, 20, 256, precision="bf16x3")
+    for Q in (256, 512):  # split operands at Q = 256 and 512: shared memory holds H <= 18
+        x = buf(20, Q, "bf16x3")
+        with pytest.raises(P.RSVDError):
+            P.align_best(x, 1, 1, x, 1, 20, Q, precision="bf16x3")
     assert P.compressed_bytes(4, 1, 8, 64, "bf16") == 0
 
 
