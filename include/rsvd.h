@@ -300,6 +300,15 @@ size_t rsvd_lse_backward_workspace_bytes(int N_A, int T, int N_B, int H, int Q);
 int rsvd_lse_backward(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
                       int precision, float inv_sigma2, const float* L, const float* gL, void* gA,
                       void* gB, void* workspace, size_t workspace_bytes, void* stream);
+/* Same as rsvd_lse_backward, except that the template gradient of this call
+ * is added to gB instead of replacing it (gA is written as before). The
+ * template gradient sums over every image, so a caller that streams the
+ * images through in batches (each batch with its own L and gL rows) gets the
+ * whole gradient by clearing gB once and accumulating every batch into it;
+ * per batch the addition is one more FP32 rounding per element. */
+int rsvd_lse_backward_accumulate(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
+                                 int precision, float inv_sigma2, const float* L, const float* gL, void* gA,
+                                 void* gB, void* workspace, size_t workspace_bytes, void* stream);
 int rsvd_compress_backward(int R, int Q, const double* k, const double* w, const double* U, int H,
                            const void* gC, int N, const double* deltas, int T, int precision,
                            void* gpolar, void* stream);

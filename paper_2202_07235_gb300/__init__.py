@@ -33,6 +33,7 @@ from .api import (  # noqa: F401
     compressed_bytes,
     lse_align,
     lse_backward,
+    lse_backward_workspace_bytes,
     lse_rows,
     pack,
     rate_probe,

@@ -42,6 +42,8 @@ SIGNATURES = {
     "rsvd_lse_backward_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "rsvd_lse_backward": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "rsvd_lse_backward_accumulate": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float,
+                                             c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rsvd_compress_backward": (c_int, [c_int, c_int, c_double_p, c_double_p, c_void_p, c_int, c_void_p, c_int,
                                        c_double_p, c_int, c_int, c_void_p, c_void_p]),
     "rsvd_align_best_pairwise": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_int, c_int, c_float,

@@ -591,19 +591,36 @@ def lse_rows(lse: torch.Tensor, stream=None) -> torch.Tensor:
     return L
 
 
-def lse_backward(cA, N_A, T, cB, N_B, H, Q, inv_sigma2, L, gL, precision: int = FP32, stream=None):
-    """Gradients (gA, gB) of sum_n gL[n] L[n] with respect to the compressed rings."""
+def lse_backward_workspace_bytes(N_A, T, N_B, H, Q) -> int:
+    return int(lib().rsvd_lse_backward_workspace_bytes(N_A, T, N_B, H, Q))
+
+
+def lse_backward(cA, N_A, T, cB, N_B, H, Q, inv_sigma2, L, gL, precision: int = FP32, stream=None,
+                 gA=None, gB=None, accumulate: bool = False, workspace=None):
+    """Gradients (gA, gB) of sum_n gL[n] L[n] with respect to the compressed rings.
+    With accumulate=True the template gradient is added to the given gB
+    (rsvd_lse_backward_accumulate: images streamed through in batches)."""
     precision = _prec(precision)
     _require_operands(cA, N_A, T, cB, N_B, H, Q, precision)
     _require_out(L, (N_A,), torch.float32, "L")
     _require_out(gL, (N_A,), torch.float32, "gL")
-    gA = torch.empty_like(cA)
-    gB = torch.empty_like(cB)
-    need = int(lib().rsvd_lse_backward_workspace_bytes(N_A, T, N_B, H, Q))
-    ws = torch.empty(max(need, 16), dtype=torch.uint8, device=cA.device)
-    check(lib().rsvd_lse_backward(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, float(inv_sigma2), _ptr(L),
-                                  _ptr(gL), _ptr(gA), _ptr(gB), _ptr(ws), ws.numel(), _stream(stream)),
-          "rsvd_lse_backward")
+    if gA is None:
+        gA = torch.empty_like(cA)
+    else:
+        _require_dev_bytes(gA, compressed_bytes(N_A, T, H, Q, precision), "gA")
+    if gB is None:
+        if accumulate:
+            raise ValueError("accumulate needs the gB to add to")
+        gB = torch.empty_like(cB)
+    else:
+        _require_dev_bytes(gB, compressed_bytes(N_B, 1, H, Q, precision), "gB")
+    need = lse_backward_workspace_bytes(N_A, T, N_B, H, Q)
+    ws = workspace if workspace is not None else torch.empty(max(need, 16), dtype=torch.uint8, device=cA.device)
+    _require_dev_bytes(ws, need, "workspace")
+    fn = lib().rsvd_lse_backward_accumulate if accumulate else lib().rsvd_lse_backward
+    check(fn(_ptr(cA), N_A, T, _ptr(cB), N_B, H, Q, precision, float(inv_sigma2), _ptr(L), _ptr(gL), _ptr(gA),
+             _ptr(gB), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+          "rsvd_lse_backward_accumulate" if accumulate else "rsvd_lse_backward")
     return gA, gB
 
 

@@ -18,14 +18,21 @@ __global__ void lse_rows_kernel(const float* __restrict__ lse, int N_A, int N_B,
   if (lane == 0) L[warp] = m + logf(s);
 }
 
-// out[i] = sum_k partial[k][i] (fixed order: deterministic).
-__global__ void sum_splits_kernel(const float2* __restrict__ partial, int nsplit, size_t n, float2* __restrict__ out) {
+// out[i] = sum_k partial[k][i] (fixed order: deterministic); with `accumulate`
+// the sum is added to out[i].
+__global__ void sum_splits_kernel(const float2* __restrict__ partial, int nsplit, size_t n, float2* __restrict__ out,
+                                  int accumulate) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     float2 acc = partial[i];
     for (int k = 1; k < nsplit; ++k) {
       const float2 v = partial[(size_t)k * n + i];
       acc.x += v.x;
       acc.y += v.y;
+    }
+    if (accumulate) {
+      const float2 o = out[i];
+      acc.x += o.x;
+      acc.y += o.y;
     }
     out[i] = acc;
   }
@@ -81,10 +88,11 @@ extern "C" size_t rsvd_lse_backward_workspace_bytes(int N_A, int T, int N_B, int
   return (size_t)ns * N_B * H * (Q / 2) * sizeof(float2);
 }
 
-extern "C" int rsvd_lse_backward(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
-                                 float inv_sigma2, const float* L, const float* gL, void* gA, void* gB, void* workspace,
-                                 size_t workspace_bytes, void* stream) {
-  using namespace rsvd;
+namespace rsvd {
+namespace {
+int lse_backward(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
+                 float inv_sigma2, const float* L, const float* gL, void* gA, void* gB, void* workspace,
+                 size_t workspace_bytes, int accumulate, void* stream) {
   int rc = check_align_args(cA, N_A, T, cB, N_B, H, Q, precision);
   if (rc != RSVD_OK) return rc;
   if (!L || !gL || !gA || !gB) return RSVD_EINVAL;
@@ -129,6 +137,22 @@ extern "C" int rsvd_lse_backward(const void* cA, int N_A, int T, const void* cB,
 
   const size_t n = (size_t)N_B * H * (Q / 2);
   sum_splits_kernel<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(
-      static_cast<const float2*>(workspace), ns, n, static_cast<float2*>(gB));
+      static_cast<const float2*>(workspace), ns, n, static_cast<float2*>(gB), accumulate);
   return launch_status();
+}
+}  // namespace
+}  // namespace rsvd
+
+extern "C" int rsvd_lse_backward(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision,
+                                 float inv_sigma2, const float* L, const float* gL, void* gA, void* gB, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+  return rsvd::lse_backward(cA, N_A, T, cB, N_B, H, Q, precision, inv_sigma2, L, gL, gA, gB, workspace,
+                            workspace_bytes, 0, stream);
+}
+
+extern "C" int rsvd_lse_backward_accumulate(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q,
+                                            int precision, float inv_sigma2, const float* L, const float* gL, void* gA,
+                                            void* gB, void* workspace, size_t workspace_bytes, void* stream) {
+  return rsvd::lse_backward(cA, N_A, T, cB, N_B, H, Q, precision, inv_sigma2, L, gL, gA, gB, workspace,
+                            workspace_bytes, 1, stream);
 }

@@ -68,7 +68,9 @@ def test_size_queries(lib):
     assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 3) == 2 * 586 * 32 * 96 * 128 * 2
     assert lib.rsvd_compressed_bytes(256, 1, 6, 128, 2) == 2 * 32 * 32 * 128 * 2           # H 6 -> 8
     assert lib.rsvd_compressed_bytes(8, 1, 5, 256, 1) == 1 * 32 * 48 * 128 * 2             # H 5 -> 6
-    assert lib.rsvd_compressed_bytes(8, 1, 12, 512, 2) == 0  # tensor-core forms: Q in {128, 256}
+    assert lib.rsvd_compressed_bytes(8, 1, 12, 512, 2) == 1 * 32 * 192 * 128 * 2  # Q = 512: g = 8, Hp even
+    assert lib.rsvd_compressed_bytes(8, 1, 7, 512, 1) == 1 * 32 * 128 * 128 * 2   # H 7 -> 8
+    assert lib.rsvd_compressed_bytes(8, 1, 12, 1024, 2) == 0  # tensor-core forms: Q in {128, 256, 512}
     assert lib.rsvd_compressed_bytes(8, 1, 33, 256, 3) == 0
     assert lib.rsvd_compressed_bytes(8, 1, 12, 256, 7) == 0
     lib.rsvd_build_workspace_bytes.restype = ctypes.c_size_t
@@ -88,7 +90,7 @@ def test_argument_errors_return_codes_without_a_gpu(lib):
     # Q not a power of two / unknown precision / tensor-core form outside its Q and H range / H too large
     assert f(one, 1, 1, one, 1, 8, 100, 0, 1.0, one, one, None, None) == -2
     assert f(one, 1, 1, one, 1, 8, 256, 5, 1.0, one, one, None, None) == -2
-    assert f(one, 1, 1, one, 1, 8, 512, 3, 1.0, one, one, None, None) == -2
+    assert f(one, 1, 1, one, 1, 8, 1024, 3, 1.0, one, one, None, None) == -2
     assert f(one, 1, 1, one, 1, 33, 256, 1, 1.0, one, one, None, None) == -2
     assert f(one, 1, 1, one, 1, 65, 256, 0, 1.0, one, one, None, None) == -2
     # log-sum-exp requested with a non-positive scale

@@ -164,6 +164,37 @@ def test_lse_align_gradient_finite_differences_fp32():
             assert abs(fd - an) <= 2e-2 * abs(an) + 1e-4, (which, fd, an)
 
 
+@pytest.mark.parametrize("Q,R,H,T_side", [(256, 64, 12, 3), (512, 48, 16, 2)])
+def test_lse_backward_accumulated_over_image_batches(Q, R, H, T_side):
+    """The images streamed through in three batches, each batch's template
+    gradient added into one gB (rsvd_lse_backward_accumulate): against the
+    oracle gradient of the whole set; the image gradients of each batch
+    against the oracle rows of that batch."""
+    N_A, N_B = 11, 6
+    wl, A, B, U = _setup(Q, R, H, T_side, N_A, N_B, seed=Q + 3 * H)
+    g = wl.grid
+    T = wl.deltas.shape[0]
+    Ut = torch.from_numpy(U).to(DEV)
+    cB = P.compress(g.k, g.w, Ut, torch.from_numpy(B).to(DEV))
+    gB = torch.zeros_like(cB)
+    gAs = []
+    for n0, n1 in ((0, 4), (4, 9), (9, 11)):
+        n = n1 - n0
+        cA = P.compress(g.k, g.w, Ut, torch.from_numpy(A[n0:n1]).to(DEV), deltas=wl.deltas)
+        _, _, lse = P.align_best(cA, n, T, cB, N_B, H, Q, want_lse=True)
+        L = P.lse_rows(lse)
+        gL = torch.ones(n, dtype=torch.float32, device=DEV)
+        gA, _ = P.lse_backward(cA, n, T, cB, N_B, H, Q, 1.0, L, gL, gB=gB, accumulate=True)
+        gAs.append(gA.cpu().numpy())
+    P.status()
+    a_c = O.compress(O.translate(A.astype(np.complex128), g.k, wl.deltas), U, g.w)
+    b_c = O.compress(B.astype(np.complex128), U, g.w)
+    _, _, G_ac, G_bc = O.lse_grad_compressed(a_c, b_c, 1.0)
+    assert _rel(gB.cpu().numpy(), pack_slots(G_bc).reshape(N_B, H, Q // 2, 2)) < GTOL
+    ref_a = pack_slots(G_ac).reshape(N_A * T, H, Q // 2, 2)
+    assert _rel(np.concatenate(gAs), ref_a) < GTOL
+
+
 def test_differentiation_workload_sampled_parity():
     """4096 images x 256 templates, 128 px, 64 rings, Q = 256, 3x3 translations,
     H = 12, sigma^2 = 1: forward and backward on the GPU; the gradient of 8
