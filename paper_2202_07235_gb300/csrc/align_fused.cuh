@@ -43,6 +43,9 @@ struct FusedParams {
   int* status;
   int N_A, T, N_B, H, IMG;
   float inv_sigma2;
+  // warp-specialised kernel only: CTA b takes image group b % ngroups against
+  // templates [c jchunk, (c+1) jchunk), c = b / ngroups (0: all templates)
+  int ngroups, jchunk;
 };
 
 template <int S>

@@ -86,8 +86,14 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
   int* abort_flag = reinterpret_cast<int*>(mbar + 2);
 
   const int tid = threadIdx.x;
-  const int H = p.H, T = p.T, N_B = p.N_B;
-  const int img0 = blockIdx.x * p.IMG;
+  // CTAs that run at the same time share one chunk of templates (sized to stay
+  // in L2): image group and template chunk of this CTA
+  const int H = p.H, T = p.T;
+  const int grp_id = p.ngroups > 0 ? (int)(blockIdx.x % (unsigned)p.ngroups) : (int)blockIdx.x;
+  const int jc0 = p.ngroups > 0 ? (int)(blockIdx.x / (unsigned)p.ngroups) * p.jchunk : 0;
+  const int N_B = p.ngroups > 0 ? min(p.jchunk, p.N_B - jc0) : p.N_B;  // templates of this CTA
+  const float2* cB = p.cB + (size_t)jc0 * H * S;
+  const int img0 = grp_id * p.IMG;
   if (img0 >= p.N_A) return;
   const int nimg = min(p.IMG, p.N_A - img0);
   const int rows_cta = nimg * T;
@@ -135,10 +141,10 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
       const uint32_t per = (uint32_t)H * S * 8;
       mbar_arrive_expect_tx(&mbar[buf], per * nb);
       if (HP == H) {
-        bulk_g2s(tbuf + (size_t)buf * TBL * HP * S, p.cB + (size_t)j0 * H * S, per * nb, &mbar[buf]);
+        bulk_g2s(tbuf + (size_t)buf * TBL * HP * S, cB + (size_t)j0 * H * S, per * nb, &mbar[buf]);
       } else {
         for (int jj = 0; jj < nb; ++jj)
-          bulk_g2s(tbuf + (size_t)(buf * TBL + jj) * HP * S, p.cB + (size_t)(j0 + jj) * H * S, per, &mbar[buf]);
+          bulk_g2s(tbuf + (size_t)(buf * TBL + jj) * HP * S, cB + (size_t)(j0 + jj) * H * S, per, &mbar[buf]);
       }
     };
     if (tid == 0) {
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
           // with several batches per pass that store was committed at least one
           // FULL sync ago, so it can be fetched now; with one batch it is
           // committed in this same iteration by another thread: fetch at commit
-          if (nbatch >= 2) fetch(m, (size_t)(img0 + il) * N_B + j0 + jj);
+          if (nbatch >= 2) fetch(m, (size_t)(img0 + il) * p.N_B + jc0 + j0 + jj);
         }
       }
       return m;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(WsCfg<S, HP>::NT, 1) ws_align_kernel(const __g
         }
         if (want_lse) lse_merge(mm, sm, rlse[pr], 1.0f);
       }
-      const size_t o = (size_t)(img0 + il) * N_B + j0 + jj;
+      const size_t o = (size_t)(img0 + il) * p.N_B + jc0 + j0 + jj;
       if (m.rmw) {
         if (!m.fetched) fetch(m, o);
         if (!(vb > m.ov)) {
@@ -410,8 +416,19 @@ int launch_ws_cfg(const FusedParams& p0, cudaStream_t stream) {
   } else {
     FusedParams p = p0;
     p.IMG = images_per_cta(C::RP, p.T);
-    const long long grid = ((long long)p.N_A + p.IMG - 1) / p.IMG;
-    if (grid > 0x7fffffffLL) return RSVD_EUNSUPPORTED;
+    const long long groups = ((long long)p.N_A + p.IMG - 1) / p.IMG;
+    // template chunks of at most 40 MB (L2 holds one chunk while the image
+    // groups running at the same time stream it), a multiple of TB templates
+    const long long tbytes = (long long)p.N_B * p.H * S * 8;
+    const long long kChunkBytes = 40ll << 20;
+    int nchunk = (int)((tbytes + kChunkBytes - 1) / kChunkBytes);
+    int jchunk = (p.N_B + nchunk - 1) / nchunk;
+    jchunk = (jchunk + C::TB - 1) / C::TB * C::TB;
+    nchunk = (p.N_B + jchunk - 1) / jchunk;
+    p.ngroups = (int)groups;
+    p.jchunk = jchunk;
+    const long long grid = groups * nchunk;
+    if (groups > 0x7fffffffLL || grid > 0x7fffffffLL) return RSVD_EUNSUPPORTED;
     if (cudaFuncSetAttribute(ws_align_kernel<S, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
         cudaSuccess)
       return RSVD_ECUDA;

@@ -101,6 +101,7 @@ CASES = [
     (512, 48, 16, 2, 5, 4),      # Q = 512
     (512, 40, 12, 3, 9, 5),      # Q = 512, H = 12: two passes per image group, three template batches
     (512, 32, 7, 1, 13, 3),      # Q = 512, H padded to 8, ragged pass
+    (512, 24, 16, 2, 3, 1300),   # Q = 512, 42.6 MB of templates: two template chunks across the grid
     (128, 24, 1, 1, 3, 3),       # H = 1
     (16, 6, 3, 1, 4, 3),         # Q = 16 (generic per-pair path)
     (1024, 20, 5, 1, 2, 3),      # Q = 1024 (generic per-pair path)
