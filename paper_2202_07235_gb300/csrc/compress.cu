@@ -15,6 +15,7 @@
 //   write    slots s = 0 .. Q/2-1 of a_t(h, q) / Q, slot 0 packing (Re a(0), Re a(Q/2)).
 #include <math.h>
 
+#include "compress_tc.cuh"
 #include "compress_v2.cuh"
 #include "operand.cuh"
 
@@ -200,6 +201,35 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
     // padding components, lanes and tiles of the operand planes are zero
     const size_t bytes = (size_t)operand_planes(precision) * (size_t)OL.plane_elems * 2;
     if (cudaMemsetAsync(out, 0, bytes, static_cast<cudaStream_t>(stream)) != cudaSuccess) return RSVD_ECUDA;
+  }
+  if (precision == RSVD_FP32 && !fits_v2) {
+    // projection on the tensor cores (compress_tc.cu): Q in {256, 512}, R <= 128, H <= 16,
+    // where the shared-memory kernel cannot hold the rings (it is the faster
+    // one where it can: 1.87 ms against 2.9 ms on the throughput workload)
+    CompressTcParams c{};
+    c.polar = p.polar;
+    c.out = p.out;
+    c.U = U;
+    c.status = p.status;
+    c.N = N;
+    c.R = R;
+    c.Q = Q;
+    c.H = H;
+    c.T = T;
+    bool uniform = k[0] > 0.0;
+    for (int r = 0; r < R && uniform; ++r) uniform = fabs(k[r] - (r + 1) * k[0]) <= 1e-9 * k[R - 1];
+    c.uniform = uniform ? 1 : 0;
+    c.dk = (float)k[0];
+    for (int r = 0; r < R; ++r) {
+      c.k[r] = p.k[r];
+      c.sw[r] = p.sw[r];
+    }
+    for (int t = 0; t < T; ++t) {
+      c.dx[t] = p.dx[t];
+      c.dy[t] = p.dy[t];
+    }
+    const int rc_tc = launch_compress_tc(c, static_cast<cudaStream_t>(stream));
+    if (rc_tc != RSVD_EUNSUPPORTED) return rc_tc;
   }
   {
     // shared-memory kernel when half of one object's rings fits (compress_v2.cu)

@@ -94,6 +94,21 @@ __device__ __forceinline__ void tc_mma_f16_by(uint32_t leader, uint32_t d_tmem, 
       : "memory");
 }
 
+// kind::tf32 (TF32 operands stored as 32-bit floats, FP32 accumulate; K = 8
+// per instruction), issued by the lane whose `leader` is non-zero.
+__device__ __forceinline__ void tc_mma_tf32_by(uint32_t leader, uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                               uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p, e;\n"
+      "setp.ne.b32 e, %5, 0;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate), "r"(leader)
+      : "memory");
+}
+
 // tcgen05.commit tracks the MMAs of the executing thread: issue it from the
 // lane that issued them.
 __device__ __forceinline__ void tc_commit_by(uint32_t leader, uint64_t* bar) {
@@ -138,8 +153,8 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lb
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, both operands K-major.
-// ab_format: 0 = fp16, 1 = bf16.
+// Instruction descriptor of kind::f16 / kind::tf32: FP32 accumulator, both
+// operands K-major. ab_format: 0 = fp16, 1 = bf16 (kind::f16), 2 = tf32 (kind::tf32).
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_format, int M, int N) {
   return (1u << 4)                        // D format: f32
          | (ab_format << 7)               // A format
@@ -315,6 +330,17 @@ __device__ __forceinline__ void tmem_wait_ld_tie<32>(uint32_t (&r)[32]) {
                  "+r"(r[30]), "+r"(r[31])
                :
                : "memory");
+}
+
+// 16 consecutive columns of the thread's lane, no wait.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
 }
 
 // Registers -> TMEM: `N` complex values (2N columns) at taddr. The caller

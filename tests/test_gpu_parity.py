@@ -32,8 +32,13 @@ def _gpu(wl, A, B, U):
 
 
 @pytest.mark.parametrize("Q,R,H,T_side", [(128, 32, 8, 1), (128, 32, 32, 1), (256, 64, 12, 3), (512, 48, 16, 2),
-                                          (16, 6, 3, 1), (1024, 20, 5, 1)])
+                                          (16, 6, 3, 1), (1024, 20, 5, 1),
+                                          # tensor-core projection (rings beyond the shared-memory kernel):
+                                          (256, 128, 16, 2), (512, 100, 11, 3), (512, 128, 16, 6)])
 def test_compress_matches_oracle(Q, R, H, T_side):
+    """Compressed rings against the oracle; R Q / 2 > 12,288 takes the
+    tensor-core projection (3xTF32), including R not a multiple of 32, H < 16
+    and 36 translations (two TMEM passes)."""
     wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=3, N_A=5, T_side=T_side, H=H, seed=Q + H)
     cA, cB, T = _gpu(wl, A, B, U)
     _, a_c, b_c = oracle_scores(wl, A, B, U)
@@ -44,6 +49,23 @@ def test_compress_matches_oracle(Q, R, H, T_side):
     for got, ref in ((got_a, ref_a), (got_b, ref_b)):
         scale = np.max(np.abs(ref), axis=(1, 2, 3), keepdims=True)
         assert np.max(np.abs(got - ref) / scale) < RTOL
+    P.status()
+
+
+def test_compress_non_uniform_rings_tensor_core_projection():
+    """Ring radii that are not equispaced through the tensor-core projection
+    (per-ring phase evaluation)."""
+    wl, A, B, U = setup(N=256, R=128, Q=512, N_B=2, N_A=2, T_side=3, H=16, seed=78)
+    g = wl.grid
+    rng = np.random.default_rng(4)
+    k = np.sort(rng.uniform(1.0, g.K, size=g.R))
+    w = rng.uniform(0.5, 2.0, size=g.R) * k
+    At = torch.from_numpy(A).to(DEV)
+    cA = P.compress(k, w, torch.from_numpy(U).to(DEV), At, deltas=wl.deltas).cpu().numpy()
+    a_c = O.compress(O.translate(A.astype(np.complex128), k, wl.deltas), U, w)
+    ref = pack_slots(a_c).reshape(2 * 9, 16, 256, 2)
+    scale = np.max(np.abs(ref), axis=(1, 2, 3), keepdims=True)
+    assert np.max(np.abs(cA - ref) / scale) < RTOL
     P.status()
 
 
