@@ -25,6 +25,7 @@
 #pragma once
 
 #include "align_fused.cuh"
+#include "ptx_sync.cuh"
 
 namespace rsvd {
 
@@ -42,7 +43,10 @@ struct GradParams {
 template <int S, int HP>
 struct GradCfg {
   static constexpr int P1 = FftSplit<S>::P1, P2 = FftSplit<S>::P2;
-  static constexpr int RT = cmax(1, cmin(3, 24 / HP));
+  // rows per thread: at Q = 512 the transforms run on 64 lanes with 4 points
+  // each (few registers), which leaves room for more resident rows; every
+  // resident row reuses each streamed template (32 KB at H = 16)
+  static constexpr int RT = (S == 256) ? cmax(1, cmin(3, 48 / HP)) : cmax(1, cmin(3, 24 / HP));
   static constexpr int EST = 4 * RT * HP + 2 * P1 + 4 * P2 + 64;
   static constexpr int G = cmax(1, cmin(cmin(6, 1024 / S), 65536 / (S * EST)));
   static constexpr int NT = S * G;
@@ -59,11 +63,50 @@ struct GradCfg {
   static constexpr bool kFits = SMEM <= 227 * 1024;
 };
 
+// One radix-4 pass of an M-point Stockham transform (in place in `data`, M / 4
+// lanes each holding 4 points; forward e^{-}, or e^{+} when kInv) by the
+// 64 threads of named barrier `bar`: the lane's inputs are data[j + (M/4) r]
+// (loaded when kLoad, else already in v), twiddled by W_M^{r (j % Ns) M / (4 Ns)}
+// (tw = W_M^k table), transformed, and written to
+// data[(j / Ns) 4 Ns + j % Ns + r Ns] when kStore (else left in v).
+template <int M, bool kInv, bool kLoad, bool kStore>
+__device__ __forceinline__ void grad_radix4_pass(float2* data, float2 (&v)[4], int j, int Ns, const float2* tw,
+                                                 int bar) {
+  constexpr int R4 = M / 4;
+  if (kLoad) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r] = data[j + R4 * r];
+    named_sync(bar, 64);  // every lane has read before any lane writes (here or in the next pass)
+  }
+  const int e = (j % Ns) * (R4 / Ns);
+#pragma unroll
+  for (int r = 1; r < 4; ++r) {
+    float2 w = tw[(r * e) & (M - 1)];
+    if (kInv) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]), a2 = cadd(v[1], v[3]), a3 = csub(v[1], v[3]);
+  const float2 ia3 = make_float2(-a3.y, a3.x);  // i a3
+  v[0] = cadd(a0, a2);
+  v[2] = csub(a0, a2);
+  v[1] = kInv ? cadd(a1, ia3) : csub(a1, ia3);
+  v[3] = kInv ? csub(a1, ia3) : cadd(a1, ia3);
+  if (kStore) {
+    const int d = (j / Ns) * 4 * Ns + j % Ns;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) data[d + r * Ns] = v[r];
+    named_sync(bar, 64);  // the pass is visible before the next one reads
+  }
+}
+
 template <int S, int HP, bool kTmpl>
 __global__ void __launch_bounds__(GradCfg<S, HP>::NT, 1) grad_kernel(const __grid_constant__ GradParams p) {
   using C = GradCfg<S, HP>;
   constexpr int M = S, Q = 2 * S, P1 = C::P1, P2 = C::P2, RP = C::RP, RT = C::RT, TB = C::TB, NT = C::NT;
   constexpr int SP = C::SP, XP = C::XP, F = P2, RR = P1 / P2, PAIRS = C::PAIRS, PG = NT / F;
+  // Q = 512: each pair's transforms run on 64 lanes (radix-4 Stockham passes),
+  // since a batch holds only RP x TB = 3 pairs there
+  constexpr bool kWideFft = (S == 256) && (NT % 64 == 0);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tbuf = reinterpret_cast<float2*>(smem_raw);  // [2][TB][HP][S] streamed objects, rows h >= H zero
@@ -94,9 +137,10 @@ __global__ void __launch_bounds__(GradCfg<S, HP>::NT, 1) grad_kernel(const __gri
     twQ[i] = make_float2(cs, sn);
   }
   for (int i = tid; i < M; i += NT) {
-    const int k1 = i / P2, t = i % P2;
+    // kWideFft: W_M^i (radix-4 passes); else W_M^{t k1} of the two-stage split
+    const int e = kWideFft ? i : (i % P2) * (i / P2);
     float sn, cs;
-    sincospif(-2.0f * (float)(t * k1) / (float)M, &sn, &cs);
+    sincospif(-2.0f * (float)e / (float)M, &sn, &cs);
     tw1[i] = make_float2(cs, sn);
   }
   for (int i = tid; i < 2 * TB * (HP - H) * S; i += NT) {
@@ -203,95 +247,165 @@ __global__ void __launch_bounds__(GradCfg<S, HP>::NT, 1) grad_kernel(const __gri
       }
       __syncthreads();  // spectra complete
 
-      // ---- per pair: X, P, and G(q) on F lanes ----
+      if constexpr (kWideFft) {
+        // ---- per pair: X, P, and G(q) on 64 lanes ----
+        constexpr int FW = 64, NSLOT = NT / FW, R4 = M / 4;
+        const int slot = tid / FW, j = tid % FW;
 #pragma unroll 1
-      for (int pb = 0; pb < PAIRS; pb += PG) {
-        const int pr = pb + tid / F;
-        const int rl = pr / TB, jj = pr % TB;
-        const bool ok = (pr < PAIRS) && (jj < nb) && (ps + rl < nres);
-        float2* sp = spec + (size_t)(pr < PAIRS ? pr : 0) * SP;
-        float2 z[P1];
-        if (ok) {
+        for (int pb = 0; pb < PAIRS; pb += NSLOT) {
+          const int pr = pb + slot;
+          if (pr < PAIRS) {  // slots without a pair skip (their barrier is not used)
+            const int rl = pr / TB, jj = pr % TB;
+            const bool ok = (jj < nb) && (ps + rl < nres);
+            float2* sp = spec + (size_t)pr * SP;
+            const int bar = 2 + slot;
+            float2 v[4];
+            // C2R pre-processing at k = j + 64 q, the inputs of the first pass
 #pragma unroll
-          for (int q1 = 0; q1 < P1; ++q1) {
-            const int k = ft + P2 * q1;
-            float2 A, B;
-            if (q1 == 0 && ft == 0) {
-              const float2 v = sp[0];
-              A = make_float2(v.x, 0.f);
-              B = make_float2(v.y, 0.f);
-            } else {
-              A = sp[k];
-              B = cconj(sp[M - k]);
+            for (int q = 0; q < 4; ++q) {
+              const int k = j + R4 * q;
+              float2 A, B;
+              if (k == 0) {
+                const float2 s0 = sp[0];
+                A = make_float2(s0.x, 0.f);
+                B = make_float2(s0.y, 0.f);
+              } else {
+                A = sp[k];
+                B = cconj(sp[M - k]);
+              }
+              const float2 d = cmul(csub(A, B), twQ[k]);
+              v[q] = ok ? make_float2(A.x + B.x - d.y, A.y + B.y + d.x) : make_float2(0.f, 0.f);
             }
-            const float2 d = cmul(csub(A, B), twQ[k]);
-            z[q1] = make_float2(A.x + B.x - d.y, A.y + B.y + d.x);
+            named_sync(bar, FW);
+            // forward transform: z(p) = X(2p) + i X(2p+1), p = j + 64 r after the last pass
+            grad_radix4_pass<M, false, false, true>(sp, v, j, 1, tw1, bar);
+            grad_radix4_pass<M, false, true, true>(sp, v, j, 4, tw1, bar);
+            grad_radix4_pass<M, false, true, true>(sp, v, j, 16, tw1, bar);
+            grad_radix4_pass<M, false, true, false>(sp, v, j, 64, tw1, bar);
+            {
+              const float Ln = kTmpl ? sL[jj] : rL[rl];
+              const float gn = kTmpl ? sG[jj] : rG[rl];
+              const float c = s2 * gn, cl = s2 * log2e, o = -Ln * log2e;
+#pragma unroll
+              for (int r = 0; r < 4; ++r)
+                v[r] = make_float2(c * exp2f(fmaf(cl, v[r].x, o)), c * exp2f(fmaf(cl, v[r].y, o)));
+            }
+            // inverse transform: Y(k) = sum_mu p(mu) e^{+2 pi i mu k / M}, k = j + 64 r
+            grad_radix4_pass<M, true, false, true>(sp, v, j, 1, tw1, bar);
+            grad_radix4_pass<M, true, true, true>(sp, v, j, 4, tw1, bar);
+            grad_radix4_pass<M, true, true, true>(sp, v, j, 16, tw1, bar);
+            grad_radix4_pass<M, true, true, true>(sp, v, j, 64, tw1, bar);
+            // G(k) = E(k) + e^{+2 pi i k / Q} O(k), E = (Y(k) + conj Y(M-k))/2, O = (Y(k) - conj Y(M-k))/(2i)
+            float2 g[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int k = j + R4 * r;
+              const float2 Yk = v[r];
+              if (k == 0) {
+                g[r] = make_float2(Yk.x + Yk.y, Yk.x - Yk.y);  // packed (G(0), G(Q/2))
+              } else {
+                const float2 Ym = cconj(sp[M - k]);
+                const float2 E = make_float2(0.5f * (Yk.x + Ym.x), 0.5f * (Yk.y + Ym.y));
+                const float2 O = make_float2(0.5f * (Yk.y - Ym.y), -0.5f * (Yk.x - Ym.x));
+                g[r] = cadd(E, cmul(O, cconj(twQ[k])));
+              }
+            }
+            named_sync(bar, FW);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sp[j + R4 * r] = g[r];
           }
-          RegDft<P1>::run(z);
-#pragma unroll
-          for (int k1 = 1; k1 < P1; ++k1) z[k1] = cmul(z[k1], tw1[k1 * P2 + ft]);
         }
-        __syncwarp();
-        if (ok) {
+      } else {
+        // ---- per pair: X, P, and G(q) on F lanes ----
+#pragma unroll 1
+        for (int pb = 0; pb < PAIRS; pb += PG) {
+          const int pr = pb + tid / F;
+          const int rl = pr / TB, jj = pr % TB;
+          const bool ok = (pr < PAIRS) && (jj < nb) && (ps + rl < nres);
+          float2* sp = spec + (size_t)(pr < PAIRS ? pr : 0) * SP;
+          float2 z[P1];
+          if (ok) {
 #pragma unroll
-          for (int k1 = 0; k1 < P1; ++k1) sp[k1 * XP + ft] = z[k1];
-        }
-        __syncwarp();
-        float2 y[RR][P2];
-        if (ok) {
-          const float Ln = kTmpl ? sL[jj] : rL[rl];
-          const float gn = kTmpl ? sG[jj] : rG[rl];
-          const float c = s2 * gn, cl = s2 * log2e, o = -Ln * log2e;
+            for (int q1 = 0; q1 < P1; ++q1) {
+              const int k = ft + P2 * q1;
+              float2 A, B;
+              if (q1 == 0 && ft == 0) {
+                const float2 v = sp[0];
+                A = make_float2(v.x, 0.f);
+                B = make_float2(v.y, 0.f);
+              } else {
+                A = sp[k];
+                B = cconj(sp[M - k]);
+              }
+              const float2 d = cmul(csub(A, B), twQ[k]);
+              z[q1] = make_float2(A.x + B.x - d.y, A.y + B.y + d.x);
+            }
+            RegDft<P1>::run(z);
 #pragma unroll
-          for (int i = 0; i < RR; ++i) {
-#pragma unroll
-            for (int tp = 0; tp < P2; ++tp) y[i][tp] = sp[(ft * RR + i) * XP + tp];
-            RegDft<P2>::run(y[i]);  // y[i][k2] = X(2p) + i X(2p+1), p = ft*RR + i + P1*k2
-#pragma unroll
-            for (int k2 = 0; k2 < P2; ++k2)
-              y[i][k2] = make_float2(c * exp2f(fmaf(cl, y[i][k2].x, o)), c * exp2f(fmaf(cl, y[i][k2].y, o)));
-            RegDft<P2, true>::run(y[i]);  // y[i][t] = sum_k2 e^{+2 pi i k2 t / P2} p(k1 + P1 k2)
+            for (int k1 = 1; k1 < P1; ++k1) z[k1] = cmul(z[k1], tw1[k1 * P2 + ft]);
           }
-        }
-        __syncwarp();
-        if (ok) {
+          __syncwarp();
+          if (ok) {
 #pragma unroll
-          for (int i = 0; i < RR; ++i)
+            for (int k1 = 0; k1 < P1; ++k1) sp[k1 * XP + ft] = z[k1];
+          }
+          __syncwarp();
+          float2 y[RR][P2];
+          if (ok) {
+            const float Ln = kTmpl ? sL[jj] : rL[rl];
+            const float gn = kTmpl ? sG[jj] : rG[rl];
+            const float c = s2 * gn, cl = s2 * log2e, o = -Ln * log2e;
 #pragma unroll
-            for (int t = 0; t < P2; ++t) sp[(ft * RR + i) * XP + t] = y[i][t];
-        }
-        __syncwarp();
-        if (ok) {
+            for (int i = 0; i < RR; ++i) {
 #pragma unroll
-          for (int k1 = 0; k1 < P1; ++k1) z[k1] = cmul(sp[k1 * XP + ft], cconj(tw1[k1 * P2 + ft]));
-          RegDft<P1, true>::run(z);  // z[s'] = Y(ft + P2 s'), Y(k) = sum_mu p(mu) e^{+2 pi i mu k / M}
-        }
-        __syncwarp();
-        if (ok) {
+              for (int tp = 0; tp < P2; ++tp) y[i][tp] = sp[(ft * RR + i) * XP + tp];
+              RegDft<P2>::run(y[i]);  // y[i][k2] = X(2p) + i X(2p+1), p = ft*RR + i + P1*k2
 #pragma unroll
-          for (int q1 = 0; q1 < P1; ++q1) sp[ft + P2 * q1] = z[q1];
-        }
-        __syncwarp();
-        if (ok) {
-          // G(k) = E(k) + e^{+2 pi i k / Q} O(k), E = (Y(k) + conj Y(M-k))/2, O = (Y(k) - conj Y(M-k))/(2i)
-#pragma unroll
-          for (int q1 = 0; q1 < P1; ++q1) {
-            const int k = ft + P2 * q1;
-            const float2 Yk = z[q1];
-            if (q1 == 0 && ft == 0) {
-              z[0] = make_float2(Yk.x + Yk.y, Yk.x - Yk.y);  // packed (G(0), G(Q/2))
-            } else {
-              const float2 Ym = cconj(sp[M - k]);
-              const float2 E = make_float2(0.5f * (Yk.x + Ym.x), 0.5f * (Yk.y + Ym.y));
-              const float2 O = make_float2(0.5f * (Yk.y - Ym.y), -0.5f * (Yk.x - Ym.x));
-              z[q1] = cadd(E, cmul(O, cconj(twQ[k])));
+              for (int k2 = 0; k2 < P2; ++k2)
+                y[i][k2] = make_float2(c * exp2f(fmaf(cl, y[i][k2].x, o)), c * exp2f(fmaf(cl, y[i][k2].y, o)));
+              RegDft<P2, true>::run(y[i]);  // y[i][t] = sum_k2 e^{+2 pi i k2 t / P2} p(k1 + P1 k2)
             }
           }
-        }
-        __syncwarp();
-        if (ok) {
+          __syncwarp();
+          if (ok) {
 #pragma unroll
-          for (int q1 = 0; q1 < P1; ++q1) sp[ft + P2 * q1] = z[q1];
+            for (int i = 0; i < RR; ++i)
+#pragma unroll
+              for (int t = 0; t < P2; ++t) sp[(ft * RR + i) * XP + t] = y[i][t];
+          }
+          __syncwarp();
+          if (ok) {
+#pragma unroll
+            for (int k1 = 0; k1 < P1; ++k1) z[k1] = cmul(sp[k1 * XP + ft], cconj(tw1[k1 * P2 + ft]));
+            RegDft<P1, true>::run(z);  // z[s'] = Y(ft + P2 s'), Y(k) = sum_mu p(mu) e^{+2 pi i mu k / M}
+          }
+          __syncwarp();
+          if (ok) {
+#pragma unroll
+            for (int q1 = 0; q1 < P1; ++q1) sp[ft + P2 * q1] = z[q1];
+          }
+          __syncwarp();
+          if (ok) {
+            // G(k) = E(k) + e^{+2 pi i k / Q} O(k), E = (Y(k) + conj Y(M-k))/2, O = (Y(k) - conj Y(M-k))/(2i)
+#pragma unroll
+            for (int q1 = 0; q1 < P1; ++q1) {
+              const int k = ft + P2 * q1;
+              const float2 Yk = z[q1];
+              if (q1 == 0 && ft == 0) {
+                z[0] = make_float2(Yk.x + Yk.y, Yk.x - Yk.y);  // packed (G(0), G(Q/2))
+              } else {
+                const float2 Ym = cconj(sp[M - k]);
+                const float2 E = make_float2(0.5f * (Yk.x + Ym.x), 0.5f * (Yk.y + Ym.y));
+                const float2 O = make_float2(0.5f * (Yk.y - Ym.y), -0.5f * (Yk.x - Ym.x));
+                z[q1] = cadd(E, cmul(O, cconj(twQ[k])));
+              }
+            }
+          }
+          __syncwarp();
+          if (ok) {
+#pragma unroll
+            for (int q1 = 0; q1 < P1; ++q1) sp[ft + P2 * q1] = z[q1];
+          }
         }
       }
       __syncthreads();  // G spectra complete
