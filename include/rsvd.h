@@ -229,7 +229,11 @@ int rsvd_compress(int R, int Q, const double* k, const double* w, const double* 
 /* Converts compressed rings written with RSVD_FP32 (N objects, T translations)
  * into the operand form of `precision` (RSVD_BF16, RSVD_FP16 or RSVD_BF16X3),
  * rounding each FP32 component to nearest (ties to even). The result equals
- * rsvd_compress called with that precision on the same input, byte for byte.
+ * rsvd_compress called with that precision on the same input byte for byte
+ * when the FP32 compression runs on the CUDA cores (R Q / 2 <= 12,288 for
+ * Q in {256, 512}, and every other Q); beyond that the FP32 compression
+ * projects on the tensor cores (3xTF32) while the operand forms are written
+ * from a CUDA-core projection, and the two agree to the forms' rounding.
  *   c32  dev, rsvd_compressed_bytes(N, T, H, Q, RSVD_FP32) bytes, 8-byte aligned
  *   out  dev, rsvd_compressed_bytes(N, T, H, Q, precision) bytes, 16-byte aligned */
 int rsvd_pack(const void* c32, int N, int T, int H, int Q, int precision, void* out, void* stream);

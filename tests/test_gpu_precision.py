@@ -96,11 +96,27 @@ def test_pack_is_bit_exact(form, Q, R, H, T_side, N_A, N_B):
     assert np.array_equal(got.cpu().numpy().view(np.uint16), exp)
 
 
+def _decode_planes(buf, N, T, H, Q, form):
+    """Operand planes (uint16) -> the represented values (hi + lo for bf16x3)."""
+    u = buf.cpu().numpy().view(np.uint16)
+    planes = 2 if form == "bf16x3" else 1
+    u = u.reshape(planes, -1)
+    if form == "fp16":
+        return u[0].view(np.float16).astype(np.float64)
+    vals = (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return vals.sum(axis=0)
+
+
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("Q,R,H", [(256, 64, 12), (512, 128, 16)])
 def test_compress_operand_form_equals_pack_of_fp32(form, Q, R, H):
-    """Q = 512 with 128 rings goes through the generic compression kernel (the
-    shared-memory kernel holds R Q / 2 <= 12,288 samples)."""
+    """Where both run the same compression kernel (the shared-memory kernel,
+    Q = 256 here) the operand form equals the pack of the FP32 compression byte
+    for byte. At Q = 512 with 128 rings the FP32 compression projects on the
+    tensor cores (3xTF32) and the operand forms on the CUDA cores, so the two
+    FP32 values differ by rounding: the represented values agree within one
+    unit in the last place of the form (2^-7 of the largest magnitude for bf16,
+    2^-10 for fp16, 2^-15 for the hi + lo pair of bf16x3)."""
     wl, A, B, U = setup(N=2 * R, R=R, Q=Q, N_B=3, N_A=17, T_side=3, H=H, seed=5)
     g = wl.grid
     At, Ut = torch.from_numpy(A).to(DEV), torch.from_numpy(U).to(DEV)
@@ -108,7 +124,14 @@ def test_compress_operand_form_equals_pack_of_fp32(form, Q, R, H):
     c16 = P.compress(g.k, g.w, Ut, At, deltas=wl.deltas, precision=form)
     ref = P.pack(c32, 17, 9, H, Q, form)
     P.status()
-    assert torch.equal(c16, ref)
+    if Q == 256:
+        assert torch.equal(c16, ref)
+        return
+    a = _decode_planes(c16, 17, 9, H, Q, form)
+    b = _decode_planes(ref, 17, 9, H, Q, form)
+    scale = np.max(np.abs(c32.cpu().numpy()))
+    tol = {"bf16": 2.0 ** -7, "fp16": 2.0 ** -10, "bf16x3": 2.0 ** -15}[form]
+    assert np.max(np.abs(a - b)) <= tol * scale
 
 
 def _gpu_form(sa, sb, N_A, T, N_B, H, Q, form):
