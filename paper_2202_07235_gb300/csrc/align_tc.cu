@@ -65,6 +65,9 @@ struct TcCfg {
   static constexpr bool kShare = NT == 1;
   static constexpr int TPT = kShare ? 1 : NT / 2;
   static constexpr int RES = kShare ? 2 : NT;  // result slots per row and tile
+  // stages per group: at Q = 512 a group's operand (K = 16 Hp components, 64 KB
+  // per plane at H = 16) arrives in two stages of half its K range (Hp even)
+  static constexpr int NSPL = Q == 512 ? 2 : 1;
 };
 
 struct TcParams {
@@ -78,7 +81,6 @@ struct TcParams {
   int* status;
   int N_A, T, N_B, IPT, nRT, nTP, CH, nUnits;
   int K, KC, KS, Hp, stages, split, lse_on, nprod;
-  int nspl;  // stages per group: the group's K-steps in nspl equal parts (KS K-steps each)
   int bres;  // template blocks of all 32 groups resident for a whole work unit (single-pass forms)
   float inv_sigma2;
   uint32_t idesc;
@@ -340,7 +342,7 @@ __device__ __forceinline__ float4 tc_pair_shared(const TcParams& p, uint32_t tl,
 template <int Q, bool kWriteX, bool kPair>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_constant__ TcParams p) {
   using C = TcCfg<Q>;
-  constexpr int g = C::g, NT = C::NT, TPT = C::TPT;
+  constexpr int g = C::g, NT = C::NT, TPT = C::TPT, NSPL = C::NSPL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(tc_smem + p.bar_off);
   uint64_t* empty = full + p.stages;
@@ -394,12 +396,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
     // every group: source word in the template rows (group 0, plane 0),
     // destination word in the block, slot-0 flag (u == 0).
     constexpr int kMaxItems = 8;  // NT * g * Hp / 32 with Hp <= 32
-    // With p.nspl = 2 an item lies in one half of the group's K range (it_kh),
+    // With NSPL = 2 an item lies in one half of the group's K range (it_kh),
     // and its destination is relative to that half's block.
     int it_src[kMaxItems], it_dst[kMaxItems];
     uint32_t it_u0 = 0u, it_kh = 0u;
     const int n_items = NT * g * p.Hp;
-    const int k_part = p.K / p.nspl;
+    const int k_part = p.K / NSPL;
 #pragma unroll
     for (int r = 0; r < kMaxItems; ++r) {
       const int i = lane + 32 * r;
@@ -485,8 +487,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
         __syncwarp();
       }
       for (int rt = rt0; rt < rt1 && ok; ++rt, ++ptile) {
-        for (int gi = 0; gi < kOpGroups * p.nspl; ++gi) {
-          const int grp = gi / p.nspl, kh = gi - grp * p.nspl;  // group, part of its K range
+        for (int gi = 0; gi < kOpGroups * NSPL; ++gi) {
+          const int grp = gi / NSPL, kh = gi - grp * NSPL;  // group, part of its K range
           const int s = ps;
           if (p.nprod == 2 && (it & 1) != mine) {
             ++it;
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           unsigned char* st = tc_smem + (size_t)s * p.stage_bytes;
           if (lane == 0) {
             mbar_arrive_expect_tx(&full[s], planes * p.a_bytes);
-            const long long off = (((long long)rt * kOpGroups + grp) * p.KC + (long long)kh * (p.KC / p.nspl)) *
+            const long long off = (((long long)rt * kOpGroups + grp) * p.KC + (long long)kh * (p.KC / NSPL)) *
                                   kOpLanes * 8;
             for (int pl = 0; pl < planes; ++pl) bulk_g2s(st + pl * p.a_bytes, p.a + pl * p.a_plane + off, p.a_bytes, &full[s]);
           }
@@ -599,8 +601,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
             ms = (s1 + 1 == p.stages) ? 0 : s1 + 1;
             mphase = (s1 + 1 == p.stages) ? (ph1 ^ 1u) : ph1;
           }
-          for (int gi = 0; !kPair && gi < kOpGroups * p.nspl; ++gi) {
-            const int grp = gi / p.nspl, kh = gi - grp * p.nspl;
+          for (int gi = 0; !kPair && gi < kOpGroups * NSPL; ++gi) {
+            const int grp = gi / NSPL, kh = gi - grp * NSPL;
             const int s = ms;
             if (!__all_sync(0xffffffffu, tc_wait(&full[s], mphase, abort_flag, p.status))) {
               ok = false;
@@ -732,17 +734,15 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   p.split = precision == RSVD_BF16X3 ? 1 : 0;
   p.K = La.K;
   p.KC = La.KC;
-  // Q = 512: a group's operand (K = 16 Hp components, 64 KB per plane at H = 16)
-  // arrives in two stages of half its K range (Hp is even there)
-  p.nspl = (Q == 512) ? 2 : 1;
-  p.KS = La.K / 16 / p.nspl;
+  constexpr int NSPL = C::NSPL;
+  p.KS = La.K / 16 / NSPL;
   p.Hp = La.Hp;
   p.IPT = La.IPT;
   p.nRT = (int)La.tiles;
   p.nTP = (p.N_B + C::NT - 1) / C::NT;
   p.idesc = idesc_f16(precision == RSVD_FP16 ? 0u : 1u, 128, 16);
-  p.a_bytes = (uint32_t)(kOpLanes * La.K * 2 / p.nspl);
-  p.b_bytes = (uint32_t)(16 * La.K * 2 / p.nspl);
+  p.a_bytes = (uint32_t)(kOpLanes * La.K * 2 / NSPL);
+  p.b_bytes = (uint32_t)(16 * La.K * 2 / NSPL);
   const uint32_t dense_bytes = (uint32_t)(planes * C::NT * kOpGroups * La.K * 2);  // per producer warp
   p.dense_bytes = dense_bytes;
   const uint32_t res_bytes = 2u * C::RES * kOpLanes * 16u;
@@ -755,7 +755,7 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   const Opt opts[] = {{1, 2, 3}, {1, 1, 3}, {0, 2, 3}, {0, 1, 2}};
   bool found = false;
   for (const Opt& o : opts) {
-    if (o.bres && (planes != 1 || p.nspl != 1)) continue;
+    if (o.bres && (planes != 1 || NSPL != 1)) continue;
     const uint32_t sb = (uint32_t)((planes * (p.a_bytes + (o.bres ? 0u : p.b_bytes)) + 1023) / 1024 * 1024);
     const uint32_t fx = (uint32_t)o.nprod * dense_bytes + (o.bres ? bres_bytes : 0u) + res_bytes + 1024u;
     if (fx < kMaxSmem && (int)((kMaxSmem - fx) / sb) >= o.min_stages) {
@@ -773,8 +773,8 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   uint32_t smem = 0;
   // with two parts per group the stage count is even, so every stage always
   // holds the same part and its template block keeps one zero pattern
-  for (; stages >= 2; stages -= (p.nspl == 2 && (stages & 1) == 0) ? 2 : 1) {
-    if (p.nspl == 2 && (stages & 1)) continue;
+  for (; stages >= 2; stages -= (NSPL == 2 && (stages & 1) == 0) ? 2 : 1) {
+    if (NSPL == 2 && (stages & 1)) continue;
     p.stages = stages;
     p.dense_off = (uint32_t)stages * p.stage_bytes;
     p.bres_off = p.dense_off + (uint32_t)p.nprod * dense_bytes;
