@@ -27,6 +27,7 @@ from .rsvd_ref import (  # noqa: F401
     lse_loss_grad,
     lse_pair_partials,
     operand_terms,
+    pow2_row_scale,
     principal_vectors,
     radial_kernel,
     radial_kernel_translated,

@@ -230,6 +230,14 @@ def compress_adjoint(G_c: np.ndarray, U: np.ndarray, w: np.ndarray, k: np.ndarra
 #           X_hat(q) = 2 pi sum_h [conj(a_hi) b_hi + conj(a_hi) b_lo + conj(a_lo) b_hi]
 #           (the compensated bf16x3 product of Henry, Tang & Heinecke,
 #           ARITH 2019; the lo*lo term is dropped).
+#   scaled split (fp16x3): the same three products with IEEE half operands after
+#           a power-of-two scaling of each operand row (one object at one
+#           translation): x_s = x 2^e with e = 14 - E, 2^(E-1) <= m < 2^E for the
+#           row's largest component magnitude m (e = 0 for a zero row), so the
+#           row's largest |x_s| lies in [2^13, 2^14); hi = rn_fp16(x_s),
+#           lo = rn_fp16(x_s - hi); the operand is (hi + lo) 2^-e. Half precision
+#           keeps 11 significant bits per part against bfloat16's 8, and the
+#           scaling keeps the parts out of its narrow exponent range's ends.
 # Only the half spectrum q = 0..Q/2 is an operand (real images: the rest is
 # its conjugate), and the q = 0 and q = Q/2 coefficients enter by their real
 # parts.
@@ -262,9 +270,20 @@ def _round_complex(z: np.ndarray, rn) -> np.ndarray:
     return rn(z.real) + 1j * rn(z.imag)
 
 
+def pow2_row_scale(z: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Power-of-two scaling of each operand row for the fp16x3 form: z [..., H, Q]
+    (one row = the leading indices) -> (z 2^e, 2^-e) with 2^-e broadcastable
+    against z, e = 14 - E where 2^(E-1) <= max |Re|, |Im| of the row < 2^E
+    (e = 0 for a zero row)."""
+    m = np.maximum(np.abs(z.real), np.abs(z.imag)).max(axis=(-2, -1), keepdims=True)
+    _, E = np.frexp(m)
+    e = np.where(m > 0, 14 - E, 0)
+    return np.ldexp(z.real, e) + 1j * np.ldexp(z.imag, e), np.ldexp(1.0, -e)
+
+
 def operand_terms(a_c: np.ndarray, b_c: np.ndarray, form: str) -> list[tuple[np.ndarray, np.ndarray]]:
     """The (image operand, template operand) pairs whose Step-1 products are
-    summed for `form` in {"fp64", "bf16", "fp16", "bf16x3"}."""
+    summed for `form` in {"fp64", "bf16", "fp16", "bf16x3", "fp16x3"}."""
     a = half_spectrum_operand(a_c)
     b = half_spectrum_operand(b_c)
     if form == "fp64":
@@ -276,6 +295,11 @@ def operand_terms(a_c: np.ndarray, b_c: np.ndarray, form: str) -> list[tuple[np.
         a_hi, b_hi = _round_complex(a, round_bf16), _round_complex(b, round_bf16)
         a_lo, b_lo = _round_complex(a - a_hi, round_bf16), _round_complex(b - b_hi, round_bf16)
         return [(a_hi, b_hi), (a_hi, b_lo), (a_lo, b_hi)]
+    if form == "fp16x3":
+        (a_s, fa), (b_s, fb) = pow2_row_scale(a), pow2_row_scale(b)
+        a_hi, b_hi = _round_complex(a_s, round_fp16), _round_complex(b_s, round_fp16)
+        a_lo, b_lo = _round_complex(a_s - a_hi, round_fp16), _round_complex(b_s - b_hi, round_fp16)
+        return [(a_hi * fa, b_hi * fb), (a_hi * fa, b_lo * fb), (a_lo * fa, b_hi * fb)]
     raise ValueError(form)
 
 

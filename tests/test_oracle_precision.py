@@ -130,3 +130,75 @@ def test_every_operand_is_a_value_of_its_format():
     for form, dtype in (("bf16", torch.bfloat16), ("fp16", torch.float16), ("bf16x3", torch.bfloat16)):
         for A, B in O.operand_terms(a, b, form):
             assert representable(A, dtype) and representable(B, dtype), form
+
+
+def test_pow2_row_scale_puts_each_row_maximum_in_one_binade():
+    """fp16x3 scaling: per row (leading indices) a power of two 2^e with the
+    row's largest component in [2^13, 2^14) after scaling, undone exactly by
+    the returned factor; a zero row keeps factor 1."""
+    rng = np.random.default_rng(12)
+    z = (rng.standard_normal((4, 3, 5, 16)) + 1j * rng.standard_normal((4, 3, 5, 16)))
+    z *= np.exp(rng.uniform(-30, 30, (4, 3, 1, 1)))
+    z[1, 2] = 0
+    zs, f = O.pow2_row_scale(z)
+    m = np.maximum(np.abs(zs.real), np.abs(zs.imag)).max(axis=(-2, -1))
+    live = np.ones((4, 3), bool)
+    live[1, 2] = False
+    assert np.all((m[live] >= 2.0**13) & (m[live] < 2.0**14))
+    assert f[1, 2, 0, 0] == 1.0 and np.all(zs[1, 2] == 0)
+    mant, _ = np.frexp(f)
+    assert np.all(mant == 0.5)  # powers of two
+    assert np.array_equal(zs * f, z)
+
+
+def test_fp16x3_parts_are_half_values_keeping_22_bits():
+    """The hi and lo parts of the scaled split are IEEE half values (torch's
+    conversion leaves them unchanged) and represent the scaled component to
+    2^-22 relative (or the half subnormal spacing 2^-24 / 2 absolute)."""
+    a, b = _small()
+    for z, terms_side in ((O.half_spectrum_operand(a), 0), (O.half_spectrum_operand(b), 1)):
+        zs, f = O.pow2_row_scale(z)
+        terms = O.operand_terms(a, b, "fp16x3")
+        hi = terms[0][terms_side] / f
+        lo = (terms[2][0] / f) if terms_side == 0 else (terms[1][1] / f)
+        for part in (hi.real, hi.imag, lo.real, lo.imag):
+            t = torch.from_numpy(np.ascontiguousarray(part)).to(torch.float32)
+            assert np.array_equal(t.to(torch.float16).to(torch.float64).numpy(), part)
+        for x, h, l in ((zs.real, hi.real, lo.real), (zs.imag, hi.imag, lo.imag)):
+            assert np.all(np.abs(x - h - l) <= np.maximum(2.0**-22 * np.abs(x), 2.0**-25))
+
+
+def test_fp16x3_is_invariant_under_power_of_two_scaling():
+    """Scaling the images by 2^k scales the fp16x3 score by exactly 2^k, far
+    outside half precision's range (the per-row scaling absorbs it)."""
+    a, b = _small()
+    X0 = O.scores_compressed_form(a, b, "fp16x3")
+    for k in (-60, -17, 23, 50):
+        assert np.array_equal(O.scores_compressed_form(a * 2.0**k, b, "fp16x3"), 2.0**k * X0), k
+        assert np.array_equal(O.scores_compressed_form(a, b * 2.0**k, "fp16x3"), 2.0**k * X0), k
+
+
+def test_fp16x3_error_is_far_below_bf16x3_and_needs_every_term():
+    a, b = _small()
+    X = O.scores_compressed(a, b).real
+    nrm = np.linalg.norm(X)
+    e3 = np.linalg.norm(O.scores_compressed_form(a, b, "fp16x3") - X) / nrm
+    eb = np.linalg.norm(O.scores_compressed_form(a, b, "bf16x3") - X) / nrm
+    assert e3 < 2e-7 and e3 < eb / 20
+    terms = O.operand_terms(a, b, "fp16x3")
+    for drop in range(3):
+        kept = [t for i, t in enumerate(terms) if i != drop]
+        Xhat = sum(2 * math.pi * np.einsum("nthq,jhq->ntjq", np.conj(A), B) for A, B in kept)
+        assert np.linalg.norm(np.fft.fft(Xhat, axis=-1).real - X) / nrm > 10 * e3, drop
+
+
+def test_fp16x3_is_exact_on_operands_representable_after_scaling():
+    """Rows whose scaled components are already half values pass through the
+    split unchanged (lo = 0): the score is the exact one."""
+    a, b = _small()
+    A, B = O.half_spectrum_operand(a), O.half_spectrum_operand(b)
+    rh = lambda z: O.round_fp16(z.real) + 1j * O.round_fp16(z.imag)
+    (As, fa), (Bs, fb) = O.pow2_row_scale(A), O.pow2_row_scale(B)
+    A16, B16 = rh(As) * fa, rh(Bs) * fb
+    X = O.scores_compressed(A16, B16).real
+    assert np.allclose(O.scores_compressed_form(A16, B16, "fp16x3"), X, rtol=0, atol=1e-13 * np.abs(X).max())
