@@ -205,7 +205,7 @@ def _form_roofline(P, fp, N_A, N_B, T, H, Q, align_ms, sm_count):
     and per-pair outputs at the HBM peak; with the tensor pipe's own figures
     and the MMA-instruction floor."""
     pairs = N_A * T * N_B
-    terms = 3 if fp == "bf16x3" else 1
+    terms = 3 if fp in ("bf16x3", "fp16x3") else 1
     gemm = pairs * 8 * H * (Q // 2 + 1) * terms
     fft = pairs * (2.5 * Q * math.log2(Q) + 2 * Q)
     nbytes = P.compressed_bytes(N_A, T, H, Q, fp) + P.compressed_bytes(N_B, 1, H, Q, fp) + N_A * N_B * 8
@@ -251,7 +251,7 @@ def _measure_forms(P, torch, grid, U, imgs, tmpl, deltas, cfg, T, K2, scores_ste
     stream = torch.cuda.current_stream()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     res = {}
-    for fp in ("bf16", "fp16", "bf16x3"):
+    for fp in ("bf16", "fp16", "bf16x3", "fp16x3"):
         try:
             cAf = torch.empty((P.compressed_bytes(N_A, T, H, Q, fp),), dtype=torch.uint8, device=dev)
             cBf = torch.empty((P.compressed_bytes(N_B, 1, H, Q, fp),), dtype=torch.uint8, device=dev)
@@ -270,7 +270,7 @@ def _measure_forms(P, torch, grid, U, imgs, tmpl, deltas, cfg, T, K2, scores_ste
                 if i is not None:
                     ev[i][2].record(stream)
 
-            for _ in range(3):
+            for _ in range(3 if K2 > 3 else 1):  # one warm-up step for steps of seconds
                 fstep()
             torch.cuda.synchronize()
             for i in range(K2):
@@ -1473,7 +1473,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="with --config large, skip the nested throughput-workload measurement")
     ap.add_argument("--n-images", type=int, default=0, help="override images per GPU (smaller runs)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"],
                     help="operand precision of the scoring contraction (tensor cores unless fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--backward", action="store_true",

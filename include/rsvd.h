@@ -61,12 +61,20 @@ enum rsvd_status_code {
  *   RSVD_BF16X3  each FP32 coefficient x split as hi = rn_bf16(x),
  *                lo = rn_bf16(x - hi); the products a_hi b_hi + a_hi b_lo + a_lo b_hi
  *                summed in FP32 on the tensor cores (about 16 significand bits)
+ *   RSVD_FP16X3  the same three products with IEEE half parts of the row-scaled
+ *                coefficient: each operand row (object n at translation t) is
+ *                scaled by 2^e, e = 14 - E where 2^(E-1) <= m < 2^E for the row's
+ *                largest component magnitude m (e clamped to [-126, 126], 0 for a
+ *                zero row), so its largest |x 2^e| lies in [2^13, 2^14);
+ *                hi = rn_fp16(x 2^e), lo = rn_fp16(x 2^e - hi); the scores are
+ *                scaled back by 2^-(e_image + e_template) before the reductions
+ *                (about 22 significand bits, whatever the inputs' scale)
  * Step 2 (the transform over q) and the reductions run in FP32 for every form.
- * The three tensor-core forms support Q in {128, 256, 512}, H <= 32, T <= 64
+ * The four tensor-core forms support Q in {128, 256, 512}, H <= 32, T <= 64
  * (else RSVD_EUNSUPPORTED) in rsvd_compress, rsvd_pack, rsvd_align_scores and
- * rsvd_align_best; scoring with RSVD_BF16X3 at Q = 256 and 512 takes H <= 18
- * (shared memory). The gradient entry points take RSVD_FP32 only. */
-enum rsvd_precision { RSVD_FP32 = 0, RSVD_BF16 = 1, RSVD_FP16 = 2, RSVD_BF16X3 = 3 };
+ * rsvd_align_best; scoring with RSVD_BF16X3 or RSVD_FP16X3 at Q = 256 and 512
+ * takes H <= 18 (shared memory). The gradient entry points take RSVD_FP32 only. */
+enum rsvd_precision { RSVD_FP32 = 0, RSVD_BF16 = 1, RSVD_FP16 = 2, RSVD_BF16X3 = 3, RSVD_FP16X3 = 4 };
 
 /* RSVD_ABI_VERSION of the loaded library. */
 int rsvd_abi_version(void);
@@ -208,9 +216,10 @@ int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, const void* tem
  * s >= 1 is a_t(h, s) and slot 0 packs the two real coefficients
  * (Re a_t(h, 0), Re a_t(h, Q/2)).
  *
- * Layout of `out` for RSVD_BF16 / RSVD_FP16 / RSVD_BF16X3 (the tensor-core
- * operand form): one plane of 16-bit floats (BF16X3: a hi plane, then a lo
- * plane of the same size). With g = Q/64 slots per group, Hp = H rounded up so
+ * Layout of `out` for RSVD_BF16 / RSVD_FP16 / RSVD_BF16X3 / RSVD_FP16X3 (the
+ * tensor-core operand form): one plane of 16-bit floats (BF16X3, FP16X3: a hi
+ * plane, then a lo plane of the same size; FP16X3 then holds one float per row,
+ * the factor 2^-e of row n*T + t, starting right after the lo plane). With g = Q/64 slots per group, Hp = H rounded up so
  * that K = 2*Hp*g is a multiple of 16 (and Hp even at Q = 512), IPT = 128/T
  * objects per tile and
  * tiles = ceil(N/IPT), a plane is the array
@@ -220,6 +229,11 @@ int rsvd_build_radial_svd_noalloc(int R, int Q, const double* w, const void* tem
  * of tile n / IPT; every other element is zero. Each [tile][group] block is
  * the 128 x K K-major operand image of one tensor-core contraction.
  * rsvd_compressed_bytes returns 0 for a size or precision outside these limits.
+ * RSVD_FP16X3 needs each row's largest component before its parts are rounded:
+ * rsvd_compress computes the RSVD_FP32 rings into a temporary of
+ * rsvd_compressed_bytes(N, T, H, Q, RSVD_FP32) bytes taken from the stream's
+ * memory pool (cudaMallocAsync / cudaFreeAsync on `stream`) and packs them as
+ * rsvd_pack does; it returns RSVD_ECUDA if that allocation fails.
  * ------------------------------------------------------------------------ */
 size_t rsvd_compressed_bytes(int N, int T, int H, int Q, int precision);
 int rsvd_compress(int R, int Q, const double* k, const double* w, const double* U, int H,
@@ -227,8 +241,10 @@ int rsvd_compress(int R, int Q, const double* k, const double* w, const double* 
                   void* stream);
 
 /* Converts compressed rings written with RSVD_FP32 (N objects, T translations)
- * into the operand form of `precision` (RSVD_BF16, RSVD_FP16 or RSVD_BF16X3),
- * rounding each FP32 component to nearest (ties to even). The result equals
+ * into the operand form of `precision` (RSVD_BF16, RSVD_FP16, RSVD_BF16X3 or
+ * RSVD_FP16X3), rounding each FP32 component (RSVD_FP16X3: each row-scaled
+ * component) to nearest (ties to even). For RSVD_FP16X3 the result equals
+ * rsvd_compress with that precision byte for byte. Otherwise it equals
  * rsvd_compress called with that precision on the same input byte for byte
  * when the FP32 compression runs on the CUDA cores (R Q / 2 <= 12,288 for
  * Q in {256, 512}, and every other Q); beyond that the FP32 compression

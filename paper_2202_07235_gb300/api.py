@@ -14,11 +14,11 @@ import torch
 from ._native import check, lib
 
 FP32 = 0
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3, "fp16x3": 4}
 
 
 def _prec(precision) -> int:
-    """Precision code from a name ("fp32", "bf16", "fp16", "bf16x3") or a code."""
+    """Precision code from a name ("fp32", "bf16", "fp16", "bf16x3", "fp16x3") or a code."""
     if isinstance(precision, str):
         return PRECISIONS[precision]
     if int(precision) not in PRECISIONS.values():

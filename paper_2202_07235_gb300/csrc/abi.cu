@@ -91,7 +91,7 @@ size_t rsvd_compressed_bytes(int N, int T, int H, int Q, int precision) {
   if (precision == RSVD_FP32) return (size_t)N * (size_t)T * (size_t)H * (size_t)(Q / 2) * 8u;
   rsvd::OperandLayout L{};
   if (!rsvd::is_operand_precision(precision) || !rsvd::make_operand_layout(N, T, H, Q, &L)) return 0;
-  return (size_t)rsvd::operand_planes(precision) * (size_t)L.plane_elems * 2u;
+  return rsvd::operand_bytes(L, precision);
 }
 
 }  // extern "C"

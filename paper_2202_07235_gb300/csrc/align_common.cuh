@@ -19,11 +19,13 @@ inline int check_align_args(const void* cA, int N_A, int T, const void* cB, int 
 }
 
 // Arguments of the tensor-core path (operand forms, operand.cuh): Q in
-// {128, 256, 512}, H <= 32, T <= 64, operand planes 16-byte aligned.
+// {128, 256, 512}, H <= 32, T <= 64, operand planes 16-byte aligned (the row
+// factors of RSVD_FP16X3 follow the planes, 16-byte aligned too).
 inline int check_tc_args(const void* cA, int N_A, int T, const void* cB, int N_B, int H, int Q, int precision) {
   if (!cA || !cB) return RSVD_EINVAL;
   if (N_A <= 0 || N_B <= 0 || T <= 0 || H <= 0 || Q <= 0) return RSVD_EINVAL;
-  if (precision != RSVD_BF16 && precision != RSVD_FP16 && precision != RSVD_BF16X3) return RSVD_EUNSUPPORTED;
+  if (precision != RSVD_BF16 && precision != RSVD_FP16 && precision != RSVD_BF16X3 && precision != RSVD_FP16X3)
+    return RSVD_EUNSUPPORTED;
   if (!(Q == 128 || Q == 256 || Q == 512) || H > 32 || T > kMaxT) return RSVD_EUNSUPPORTED;
   if (((uintptr_t)cA & 15u) || ((uintptr_t)cB & 15u)) return RSVD_EINVAL;
   if ((long long)N_A * T > 0x7fffffffLL / 2) return RSVD_EUNSUPPORTED;

@@ -1,5 +1,6 @@
 // Tensor-core scoring for the reduced-precision operand forms (operand.cuh):
-// rsvd_align_best and rsvd_align_scores with RSVD_BF16, RSVD_FP16, RSVD_BF16X3.
+// rsvd_align_best and rsvd_align_scores with RSVD_BF16, RSVD_FP16, RSVD_BF16X3,
+// RSVD_FP16X3.
 //
 // Eq. (image_innerproduct_pm):
 //   Step 1  X_hat(q) = 2 pi sum_h conj(a_h(q)) b_h(q)      -> tcgen05.mma into TMEM
@@ -73,6 +74,10 @@ struct TcCfg {
 struct TcParams {
   const uint16_t* a;  // image operand planes (hi, then lo)
   const uint16_t* b;  // template operand planes
+  // RSVD_FP16X3: factors 2^-e of the image rows (n T + t) and of the templates
+  // (null for the other forms)
+  const float* sA;
+  const float* sB;
   long long a_plane, b_plane;
   float* best;
   int32_t* arg;
@@ -249,10 +254,11 @@ __device__ __forceinline__ void tc_first_stage(const TcParams& p, uint32_t tl, u
 // X instead when kWriteX.
 template <int Q, bool kWriteX, int P1B, int P1E>
 __device__ __forceinline__ float4 tc_second_stage(const TcParams& p, uint32_t tl, uint32_t cb, bool row_ok,
-                                                  float* xrow) {
+                                                  float* xrow, float sc) {
   constexpr int g = TcCfg<Q>::g;
   constexpr float kTwoPi = 6.283185307179586f;
-  const float cs = kTwoPi * p.inv_sigma2;
+  // sc: the pair's power-of-two factor (RSVD_FP16X3), exact on every value
+  const float cs = kTwoPi * p.inv_sigma2 * sc, xs = kTwoPi * sc;
   float best = -INFINITY, lm = -INFINITY, ls = 0.0f;
   int bm = 0;
 #pragma unroll
@@ -274,7 +280,7 @@ __device__ __forceinline__ float4 tc_second_stage(const TcParams& p, uint32_t tl
       if (row_ok) {
 #pragma unroll
         for (int p2 = 0; p2 < 32; ++p2)
-          *reinterpret_cast<float2*>(xrow + 2 * (p1 + g * p2)) = make_float2(kTwoPi * z[p2].x, kTwoPi * z[p2].y);
+          *reinterpret_cast<float2*>(xrow + 2 * (p1 + g * p2)) = make_float2(xs * z[p2].x, xs * z[p2].y);
       }
     } else {
       float v[64];
@@ -300,7 +306,7 @@ __device__ __forceinline__ float4 tc_second_stage(const TcParams& p, uint32_t tl
       }
     }
   }
-  return make_float4(best, __int_as_float(bm), lm, ls);
+  return make_float4(best * sc, __int_as_float(bm), lm, ls);
 }
 
 // Step 2 and the per-row reduction for one (image row, template jj) pair by
@@ -309,12 +315,13 @@ __device__ __forceinline__ float4 tc_second_stage(const TcParams& p, uint32_t tl
 //   Z(k) = [X_hat(k) + conj X_hat(M - k)] + i W_Q^k [X_hat(k) - conj X_hat(M - k)],
 // split as M = g x 32 (see the file header).
 template <int Q, bool kWriteX>
-__device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj, bool row_ok, float* xrow) {
+__device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj, bool row_ok, float* xrow,
+                                          float sc) {
   constexpr int g = TcCfg<Q>::g;
   const uint32_t cb = (uint32_t)(jj * 2 * g);
   tc_first_stage<Q, 0, 17>(p, tl, cb);
   tmem_wait_st();
-  return tc_second_stage<Q, kWriteX, 0, g>(p, tl, cb, row_ok, xrow);
+  return tc_second_stage<Q, kWriteX, 0, g>(p, tl, cb, row_ok, xrow, sc);
 }
 
 // The same at Q = 512 (one template per tile) shared by the two warps of a
@@ -323,7 +330,8 @@ __device__ __forceinline__ float4 tc_pair(const TcParams& p, uint32_t tl, int jj
 // stages every epilogue thread meets at a named barrier. Returns the partial
 // reduction over this warp's angles.
 template <int Q, bool kWriteX>
-__device__ __forceinline__ float4 tc_pair_shared(const TcParams& p, uint32_t tl, int sub, bool row_ok, float* xrow) {
+__device__ __forceinline__ float4 tc_pair_shared(const TcParams& p, uint32_t tl, int sub, bool row_ok, float* xrow,
+                                                 float sc) {
   constexpr int g = TcCfg<Q>::g;
   static_assert(g == 8, "shared pairs are laid out for g = 8");
   if (sub == 0) tc_first_stage<Q, 0, 9>(p, tl, 0);
@@ -332,8 +340,8 @@ __device__ __forceinline__ float4 tc_pair_shared(const TcParams& p, uint32_t tl,
   tc_fence_before();
   named_sync(kBarEpiStage, kEpiThreads);
   tc_fence_after();
-  if (sub == 0) return tc_second_stage<Q, kWriteX, 0, g / 2>(p, tl, 0, row_ok, xrow);
-  return tc_second_stage<Q, kWriteX, g / 2, g>(p, tl, 0, row_ok, xrow);
+  if (sub == 0) return tc_second_stage<Q, kWriteX, 0, g / 2>(p, tl, 0, row_ok, xrow, sc);
+  return tc_second_stage<Q, kWriteX, g / 2, g>(p, tl, 0, row_ok, xrow, sc);
 }
 
 // kPair: single-pass forms with resident template blocks (the producers only
@@ -669,10 +677,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_align_kernel(const __grid_co
           const int j = tp * NT + jj;
           float* xrow = nullptr;
           if (kWriteX) xrow = p.X + ((n * p.T + t) * (long long)p.N_B + j) * (Q);
+          const bool ok = row_ok && j < p.N_B;
+          const float sc = (p.sA != nullptr && ok) ? p.sA[n * p.T + t] * p.sB[j] : 1.0f;
           if constexpr (C::kShare) {
-            r[i] = tc_pair_shared<Q, kWriteX>(p, tl, sub, row_ok && j < p.N_B, xrow);
+            r[i] = tc_pair_shared<Q, kWriteX>(p, tl, sub, ok, xrow, sc);
           } else {
-            r[i] = tc_pair<Q, kWriteX>(p, tl, jj, row_ok && j < p.N_B, xrow);
+            r[i] = tc_pair<Q, kWriteX>(p, tl, jj, ok, xrow, sc);
           }
         }
         tc_fence_before();
@@ -731,7 +741,7 @@ template <int Q>
 int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision, cudaStream_t stream) {
   using C = TcCfg<Q>;
   const int planes = operand_planes(precision);
-  p.split = precision == RSVD_BF16X3 ? 1 : 0;
+  p.split = is_split_precision(precision) ? 1 : 0;
   p.K = La.K;
   p.KC = La.KC;
   constexpr int NSPL = C::NSPL;
@@ -740,7 +750,7 @@ int launch_tc(TcParams& p, bool write_x, const OperandLayout& La, int precision,
   p.IPT = La.IPT;
   p.nRT = (int)La.tiles;
   p.nTP = (p.N_B + C::NT - 1) / C::NT;
-  p.idesc = idesc_f16(precision == RSVD_FP16 ? 0u : 1u, 128, 16);
+  p.idesc = idesc_f16((precision == RSVD_FP16 || precision == RSVD_FP16X3) ? 0u : 1u, 128, 16);
   p.a_bytes = (uint32_t)(kOpLanes * La.K * 2 / NSPL);
   p.b_bytes = (uint32_t)(16 * La.K * 2 / NSPL);
   const uint32_t dense_bytes = (uint32_t)(planes * C::NT * kOpGroups * La.K * 2);  // per producer warp
@@ -832,6 +842,10 @@ RSVD_HIDDEN int align_tc(const void* cA, int N_A, int T, const void* cB, int N_B
   p.b = static_cast<const uint16_t*>(cB);
   p.a_plane = La.plane_elems;
   p.b_plane = Lb.plane_elems;
+  if (precision == RSVD_FP16X3) {
+    p.sA = reinterpret_cast<const float*>(static_cast<const unsigned char*>(cA) + operand_scale_offset(La, precision));
+    p.sB = reinterpret_cast<const float*>(static_cast<const unsigned char*>(cB) + operand_scale_offset(Lb, precision));
+  }
   p.best = best;
   p.arg = arg;
   p.lse = lse;

@@ -170,6 +170,18 @@ extern "C" int rsvd_compress(int R, int Q, const double* k, const double* w, con
   }
   if (((uintptr_t)polar & 7u) || ((uintptr_t)out & 15u) || ((uintptr_t)U & 7u)) return RSVD_EINVAL;
   if ((size_t)N * T > (size_t)INT32_MAX / 2) return RSVD_EUNSUPPORTED;
+  if (precision == RSVD_FP16X3) {
+    // the row scaling needs each row's largest component before any part is
+    // rounded: FP32 rings into a stream-ordered temporary, then the scaled pack
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* tmp = nullptr;
+    if (cudaMallocAsync(&tmp, (size_t)N * T * H * (Q / 2) * 8, st) != cudaSuccess) return RSVD_ECUDA;
+    int rc32 = rsvd_compress(R, Q, k, w, U, H, polar, N, deltas, T, RSVD_FP32, tmp, stream);
+    if (rc32 == RSVD_OK)
+      rc32 = launch_pack_operands(static_cast<const float2*>(tmp), N, OL, RSVD_FP16X3, static_cast<uint16_t*>(out), st);
+    const cudaError_t fe = cudaFreeAsync(tmp, st);
+    return (rc32 == RSVD_OK && fe != cudaSuccess) ? RSVD_ECUDA : rc32;
+  }
 
   CompressParams p{};
   p.polar = static_cast<const float2*>(polar);

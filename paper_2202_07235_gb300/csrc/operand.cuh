@@ -7,6 +7,11 @@
 //   RSVD_BF16   hi = rn_bf16(x)                     (1 plane)
 //   RSVD_FP16   hi = rn_fp16(x)                     (1 plane)
 //   RSVD_BF16X3 hi = rn_bf16(x), lo = rn_bf16(x - hi)  (2 planes: hi, then lo)
+//   RSVD_FP16X3 x_s = x 2^e, hi = rn_fp16(x_s), lo = rn_fp16(x_s - hi)  (2 planes),
+//               e per operand row (object, translation) from the row's largest
+//               component m: e = 14 - E with 2^(E-1) <= m < 2^E, clamped to
+//               [-126, 126] (e = 0 for a zero row); after the planes, one FP32
+//               factor 2^-e per row (row n T + t)
 // with x the FP32 coefficient.
 //
 // Geometry (G = 32 column groups, g = Q/64 slots per group, G * g = Q/2):
@@ -38,14 +43,24 @@ struct OperandLayout {
   int K;    // components per (row, group)
   int KC;   // K / 8
   int IPT;  // objects per 128-row tile
+  long long N;  // objects
   long long tiles;
   long long plane_elems;  // 16-bit elements per plane
 };
 
 inline bool is_operand_precision(int precision) {
-  return precision == RSVD_BF16 || precision == RSVD_FP16 || precision == RSVD_BF16X3;
+  return precision == RSVD_BF16 || precision == RSVD_FP16 || precision == RSVD_BF16X3 || precision == RSVD_FP16X3;
 }
-inline int operand_planes(int precision) { return precision == RSVD_BF16X3 ? 2 : 1; }
+inline bool is_split_precision(int precision) { return precision == RSVD_BF16X3 || precision == RSVD_FP16X3; }
+inline int operand_planes(int precision) { return is_split_precision(precision) ? 2 : 1; }
+// Byte offset of the row factors (RSVD_FP16X3) and the form's total size.
+inline size_t operand_scale_offset(const OperandLayout& L, int precision) {
+  return (size_t)operand_planes(precision) * (size_t)L.plane_elems * 2u;
+}
+inline size_t operand_bytes(const OperandLayout& L, int precision) {
+  const size_t rows = precision == RSVD_FP16X3 ? (size_t)L.N * (size_t)L.T : 0u;
+  return operand_scale_offset(L, precision) + (rows * 4u + 15u) / 16u * 16u;
+}
 
 // Layout of N objects x T translations; false if (Q, T, H) is outside the
 // tensor-core path (Q in {128, 256, 512}, T <= 64, H <= 32).
@@ -62,6 +77,7 @@ inline bool make_operand_layout(long long N, int T, int H, int Q, OperandLayout*
   L->K = 2 * L->Hp * L->g;
   L->KC = L->K / 8;
   L->IPT = kOpLanes / T;
+  L->N = N;
   L->tiles = (N + L->IPT - 1) / L->IPT;
   L->plane_elems = L->tiles * kOpGroups * (long long)L->K * kOpLanes;
   return true;
@@ -97,7 +113,7 @@ __device__ __forceinline__ void operand_put(uint16_t* planes, long long plane_el
 }
 
 // Packs FP32 compressed rings (layout of rsvd_compress with RSVD_FP32) into
-// the operand planes (operand.cu).
+// the operand form (planes, and the row factors of RSVD_FP16X3) (operand.cu).
 RSVD_HIDDEN int launch_pack_operands(const float2* c32, long long N, const OperandLayout& L, int precision,
                                      uint16_t* out, cudaStream_t stream);
 

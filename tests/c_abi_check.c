@@ -31,6 +31,9 @@ int main(void) {
   CHECK(rsvd_compressed_bytes(0, 9, 12, 256, RSVD_FP32) == 0);
   /* the split form holds two bf16 planes: twice the single-pass form */
   CHECK(rsvd_compressed_bytes(4, 9, 12, 256, RSVD_BF16X3) == 2 * rsvd_compressed_bytes(4, 9, 12, 256, RSVD_BF16));
+  /* the scaled half split: two fp16 planes, then one float factor per row (16-byte padded) */
+  CHECK(rsvd_compressed_bytes(4, 9, 12, 256, RSVD_FP16X3) ==
+        rsvd_compressed_bytes(4, 9, 12, 256, RSVD_BF16X3) + (size_t)((4 * 9 * 4 + 15) / 16 * 16));
   CHECK(rsvd_build_workspace_bytes(64, 256, 1024) > 0);
   CHECK(rsvd_align_host_workspace_bytes(64, 256, 12, 9, 1024, 0, RSVD_FP32, 0) == 0); /* chunk 0 */
 

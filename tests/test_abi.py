@@ -66,6 +66,9 @@ def test_size_queries(lib):
     # operand forms: planes x tiles x 32 groups x K x 128 lanes x 2 bytes, K = 2 Hp (Q/64)
     assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 1) == 586 * 32 * 96 * 128 * 2      # 14 images / tile
     assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 3) == 2 * 586 * 32 * 96 * 128 * 2
+    # scaled half split: the two planes, then a float factor per row (N T), padded to 16 bytes
+    assert lib.rsvd_compressed_bytes(8192, 9, 12, 256, 4) == 2 * 586 * 32 * 96 * 128 * 2 + 8192 * 9 * 4
+    assert lib.rsvd_compressed_bytes(3, 1, 12, 256, 4) == 2 * 1 * 32 * 96 * 128 * 2 + 16
     assert lib.rsvd_compressed_bytes(256, 1, 6, 128, 2) == 2 * 32 * 32 * 128 * 2           # H 6 -> 8
     assert lib.rsvd_compressed_bytes(8, 1, 5, 256, 1) == 1 * 32 * 48 * 128 * 2             # H 5 -> 6
     assert lib.rsvd_compressed_bytes(8, 1, 12, 512, 2) == 1 * 32 * 192 * 128 * 2  # Q = 512: g = 8, Hp even
