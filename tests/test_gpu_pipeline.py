@@ -39,6 +39,7 @@ def _device_path(wl, A, B, U, precision, want_lse):
     (256, 64, 12, 3, 10, 7, 4, "fp32", True),      # with log-sum-exp
     (128, 32, 8, 1, 50, 16, 50, "fp32", False),    # one chunk
     (128, 32, 8, 1, 41, 9, 7, "bf16", False),      # tensor-core operands, six chunks
+    (256, 64, 12, 3, 23, 6, 8, "fp16x3", True),    # row-scaled split: per-chunk compression, row factors
     (512, 48, 16, 2, 9, 5, 2, "fp32", False),      # Q = 512, T = 4
 ])
 def test_host_pipeline_equals_device_path(Q, R, H, T_side, N_A, N_B, chunk, precision, want_lse):
