@@ -52,16 +52,44 @@ int tmpl_rows(int Q, int HP) {
   return 0;
 }
 
-// Splits of the image rows for the template gradient: enough CTAs to fill
-// the GPU about twice, each split at least 64 rows.
+// SMs of the current device (152 on GB300 when the query is unavailable, e.g.
+// a size query on a host without a GPU; the launch and its workspace query
+// then agree as long as they run on the same device).
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0) {
+    (void)cudaGetLastError();
+    return 152;
+  }
+  return sms;
+}
+
+// Splits of the image rows for the template gradient (one CTA per split and
+// group of resident templates, one CTA per SM): at least enough CTAs to fill
+// the GPU twice, each split at least 64 rows, and among up to four times that
+// many splits the first whose CTAs fill their last wave to 95 % (else the
+// fullest): 64 groups x 5 splits on 152 SMs left the third wave 11 % full.
 int choose_splits(int rows, int N_B, int Q, int HP) {
   const int rp = tmpl_rows(Q, HP);
   if (rp <= 0) return 0;
-  const int groups = (N_B + rp - 1) / rp;
-  int ns = (2 * 152 + groups - 1) / groups;
-  ns = ns < 1 ? 1 : ns;
+  const int sms = device_sms();
+  const long long groups = (N_B + rp - 1) / rp;
   const int cap = rows / 64 > 1 ? rows / 64 : 1;
-  return ns < cap ? ns : cap;
+  int ns0 = (int)((2LL * sms + groups - 1) / groups);
+  ns0 = ns0 < 1 ? 1 : (ns0 < cap ? ns0 : cap);
+  int best = ns0;
+  double best_fill = 0.0;
+  for (int ns = ns0; ns <= 4 * ns0 && ns <= cap; ++ns) {
+    const long long ctas = groups * ns, waves = (ctas + sms - 1) / sms;
+    const double fill = (double)ctas / (double)(waves * sms);
+    if (fill > best_fill + 1e-9) {
+      best = ns;
+      best_fill = fill;
+    }
+    if (fill >= 0.95) break;
+  }
+  return best;
 }
 
 }  // namespace
