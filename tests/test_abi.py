@@ -82,6 +82,21 @@ def test_size_queries(lib):
     assert lib.rsvd_build_workspace_bytes(0, 256, 1024) == 0
 
 
+def test_template_gradient_splits_fill_whole_waves(lib):
+    """The template-gradient workspace holds one partial gradient per split of
+    the image rows; the split count fills the last wave of one-CTA-per-SM
+    launches (152 SMs, the count the size query assumes without a GPU).
+    Differentiation workload: 64 groups of 4 resident templates x 7 splits =
+    448 CTAs (98 % of three waves), not x 5 (320 CTAs, a third wave 11 % full).
+    Large workload: 1,366 groups x 1 split."""
+    f = lib.rsvd_lse_backward_workspace_bytes
+    f.restype = ctypes.c_size_t
+    f.argtypes = [ctypes.c_int] * 5
+    assert f(4096, 9, 256, 12, 256) == 7 * 256 * 12 * 128 * 8
+    assert f(8192, 25, 4096, 16, 512) == 1 * 4096 * 16 * 256 * 8
+    assert f(0, 9, 256, 12, 256) == 0
+
+
 def test_argument_errors_return_codes_without_a_gpu(lib):
     from paper_2202_07235_gb300._native import SIGNATURES
 
