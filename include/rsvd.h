@@ -18,7 +18,9 @@
  *   1 <= T <= 64.
  * - "dev" pointers are device memory of the current CUDA device, "host"
  *   pointers are host memory read during the call. The caller allocates and
- *   owns every buffer; the library allocates no memory.
+ *   owns every buffer; the library allocates no memory, with one exception:
+ *   rsvd_compress (and the host-input pipelines) with RSVD_FP16X3 take a
+ *   stream-ordered temporary from the stream's memory pool (see rsvd_compress).
  * - stream is a cudaStream_t (NULL = legacy default stream). Every call only
  *   enqueues work on that stream and returns; host arrays are consumed
  *   before the call returns. Outputs are valid once the stream reaches the
